@@ -1,0 +1,167 @@
+"""Whole-run pins of the REWL oracle (Sec. 2, Eq. 1; Sec. 3, Eq. 2).
+
+* prep leaves every walker inside its window with a consistent bin;
+* the ln f schedule halves until below ln f_final;
+* converged runs reproduce exact g(E) (enumeration / Kaufman) within the
+  statistical error, with and without replica exchange, for Ising and Potts;
+* detailed balance of moves + exchanges with nearly frozen, window-specific ln g:
+  the visit histograms follow exp(-tilt) exactly as the exchange rule requires;
+* joining reproduces an exact g(E) cut into shifted windows to round-off, and picks
+  the bin where the derivatives agree.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import exact_dos as X
+
+
+def _exact(model, L, q=2):
+    ex = np.array(X.exact_lng(model, L, q))
+    return X.normalise_lng(ex, L * L * math.log(q))
+
+
+def test_prep_puts_walkers_in_windows():
+    for model, L, h in [(0, 16, 8), (10, 12, 8), (3, 8, 4)]:
+        r = O.REWL(model, L, h, 0.75, 3, 1e-3, 0.8, seed=42 + model, interval=100)
+        assert r.init() == 0
+        st = r.state()
+        N = L * L
+        for g in range(h * 3):
+            w = g // 3
+            E = O.energy(model, L, st["spins"][g])
+            kb = (E + 2 * N) // (4 if model == 0 else 1)
+            assert st["k"][g] == kb and r.lo[w] <= kb <= r.hi[w]
+        assert np.all(st["step"] == 0)
+
+
+def test_lnf_schedule_halving():
+    r = O.REWL(0, 4, 2, 0.75, 2, 1e-6, 0.8, seed=5, interval=500)
+    assert r.init() == 0
+    r.run(10 ** 6)
+    st = r.state()
+    # ln f = 2^0 ... 2^-19 are run (>= 1e-6); 2^-20 < 1e-6 ends the window
+    assert np.all(st["finished"] == 1)
+    assert np.all(st["iter"] == 20) and np.all(st["lnf"] == 2.0 ** -20)
+    # a finished window keeps its walkers identical (averaged, then frozen)
+    lng = st["lng"].reshape(2, 2, -1)
+    assert np.array_equal(lng[:, 0], lng[:, 1])
+
+
+@pytest.mark.parametrize("model,L,q,h,m,tol", [(0, 4, 2, 1, 8, 0.12), (0, 4, 2, 3, 6, 0.12),
+                                              (3, 3, 3, 2, 6, 0.25), (2, 4, 2, 2, 6, 0.12)])
+def test_converges_to_exact(model, L, q, h, m, tol):
+    ex = _exact(model, L, q)
+    fin = np.isfinite(ex)
+    errs, bias = [], np.zeros(len(ex))
+    for seed in range(4):
+        r = O.REWL(model, L, h, 0.75, m, 1e-6, 0.8, seed=1000 + seed, interval=200)
+        assert r.init() == 0
+        r.run(10 ** 7)
+        out, _ = r.stitch(0)
+        assert np.array_equal(np.isfinite(out), fin)
+        d = np.where(fin, out - np.where(fin, ex, 0), 0)
+        errs.append(np.abs(d).max())
+        bias += d / 4
+    assert max(errs) < tol, errs
+    assert np.abs(bias).max() < tol / 2, bias
+
+
+def test_ising_8x8_config1_shape():
+    ex = _exact(0, 8)
+    fin = np.isfinite(ex)
+    r = O.REWL(0, 8, 4, 0.75, 1, 1e-6, 0.8, seed=0x5EED201400000000 + 1000, interval=10_000)
+    assert r.init() == 0
+    r.run(10 ** 6)
+    out, joins = r.stitch(0)
+    st = r.state()
+    assert np.all(st["finished"] == 1)
+    err = np.abs(out[fin] - ex[fin]).max()
+    assert err < 0.5  # one walker per window: WL error saturates at O(0.1)
+    acc = st["swap_acc"][:3] / st["swap_att"][:3]
+    assert np.all((acc > 0.2) & (acc < 0.9))
+    assert all(r.lo[w + 1] <= joins[w] <= r.hi[w] for w in range(3))
+
+
+def test_detailed_balance_of_moves_and_exchanges():
+    """Windows with fixed, window-specific ln g: stationary histograms follow exp(-tilt).
+
+    With ln g_w(k) = ln g(k) + t_w k and ln f ~ 0, the WL move rule samples bin k of window
+    w with weight g(k) / g_w(k) = exp(-t_w k).  An exchange rule that breaks detailed
+    balance (wrong sign, missing term, swapped operand) distorts these histograms.
+    """
+    L, h, m = 4, 2, 2
+    ex = np.array(X.exact_lng(0, L))
+    fin = np.isfinite(ex)
+    tilt = [0.15, -0.2]
+    # flatness 2.0 is never reached, so ln g stays put (ln f = 1e-13 is negligible)
+    r2 = O.REWL(0, L, h, 0.75, m, 1e-14, 2.0, seed=77, interval=3, lnf_init=1e-13)
+    lo, hi, W = r2.lo, r2.hi, r2.W
+    lng = np.zeros((h * m, W))
+    for g in range(h * m):
+        w = g // m
+        ks = np.arange(lo[w], hi[w] + 1)
+        lng[g, : len(ks)] = np.where(fin[ks], ex[np.where(fin[ks], ks, 0)], 0.0) + tilt[w] * ks
+    assert r2.init() == 0
+    r2.put(lng=lng)
+    r2.run(120_000)
+    st = r2.state()
+    assert np.all(st["swap_acc"][:1] > 1000)
+    for w in range(h):
+        ks = np.arange(lo[w], hi[w] + 1)
+        Hs = st["H"][w * m:(w + 1) * m, : len(ks)].sum(axis=0).astype(float)
+        valid = fin[ks]
+        p = np.exp(-tilt[w] * ks) * valid
+        p /= p.sum()
+        n = Hs.sum()
+        chi2 = (((Hs - n * p) ** 2) / np.where(valid, n * p, 1.0))[valid].sum()
+        dof = valid.sum() - 1
+        # visits are correlated (moves change k by at most 2); allow a wide but finite band
+        assert chi2 / dof < 40, (w, chi2, dof)
+        # the mean bin must match exp(-tilt) weighting closely
+        kbar = (Hs * ks).sum() / n
+        kexp = (p * ks).sum()
+        assert abs(kbar - kexp) < 0.05 * (hi[w] - lo[w]), (w, kbar, kexp)
+
+
+def test_stitch_reproduces_exact_windows():
+    ex = np.array(X.exact_lng(0, 8))
+    fin = np.isfinite(ex)
+    B, h = 64, 4
+    lo, hi = O.windows(B, h, 0.75)
+    W = int((hi - lo).max() + 1)
+    lngw = np.zeros((h, W))
+    valid = np.zeros((h, W), np.uint8)
+    rng = np.random.default_rng(3)
+    for w in range(h):
+        ks = np.arange(lo[w], hi[w] + 1)
+        off = rng.normal(0, 50)
+        lngw[w, : len(ks)] = np.where(fin[ks], ex[np.where(fin[ks], ks, 0)], 0) + off
+        valid[w, : len(ks)] = fin[ks]
+    out, joins = O.stitch(0, 8, lo, hi, lngw, valid, norm=0)
+    want = X.normalise_lng(ex, 64 * math.log(2))
+    assert np.array_equal(np.isfinite(out), fin)
+    assert np.abs(out[fin] - want[fin]).max() < 1e-11
+    out1, _ = O.stitch(0, 8, lo, hi, lngw, valid, norm=1)
+    assert out1[0] == pytest.approx(math.log(2), abs=1e-12)
+    assert np.abs((out1 - out1[0])[fin] - (ex - ex[0])[fin]).max() < 1e-11
+
+
+def test_stitch_picks_bin_where_derivatives_agree():
+    # window 1 = window 0 + c (k - k0)^2: the 5-point stencil is exact on quadratics,
+    # so |beta_0 - beta_1| = 2c|k - k0|/dE vanishes exactly at k0
+    B, h = 64, 2
+    lo, hi = O.windows(B, h, 0.75)
+    W = int((hi - lo).max() + 1)
+    base = np.sin(np.arange(B + 1) * 0.1) * 20 + np.arange(B + 1) * 0.3
+    lngw = np.zeros((h, W))
+    valid = np.zeros((h, W), np.uint8)
+    k0 = 30
+    for w in range(h):
+        ks = np.arange(lo[w], hi[w] + 1)
+        lngw[w, : len(ks)] = base[ks] + (0.01 * (ks - k0) ** 2 if w == 1 else 0)
+        valid[w, : len(ks)] = 1
+    out, joins = O.stitch(0, 8, lo, hi, lngw, valid, norm=1)
+    assert list(joins) == [k0]
