@@ -1,0 +1,284 @@
+#!/usr/bin/env python
+"""Benchmark of the REWL hot path: Wang-Landau flip attempts per second.
+
+Workload (default): 2D Ising L=64, periodic, 32 windows at 75% overlap x 16 walkers per window
+(512 walkers), flatness 0.8, ln f from 1 halving towards 1e-8, 10^4 moves per walker between
+flatness checks / replica exchanges; lattices from a seeded uniform +-1 start.  One step is one
+round of the whole hot path: 10^4 WL moves per walker (+ ln g / H updates), the flatness test
+and window advance, and the replica exchange.
+
+Timing: W untimed warm-up rounds, then K rounds, each bracketed by CUDA events on the stream
+the kernels run on, with the 129 MB L2 flushed (256 MB write) before every timed round.  The
+move kernel is additionally timed on its own (events inside the library) for the roofline.
+`e2e` repeats the K rounds through the blocking public call (rewl_run) and reads the window
+ln g back to the host every round.  The CPU baseline is the C oracle on the host cores.
+
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no collective on
+the data path); value = attempts of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "ising_L64_h32_m16": dict(model=0, L=64, windows=32, walkers=16, overlap=0.75,
+                              lnf_final=1e-8, flatness=0.8, interval=10_000, config_id=2),
+    "potts10_L40_h64_m16": dict(model=10, L=40, windows=64, walkers=16, overlap=0.75,
+                                lnf_final=1e-8, flatness=0.8, interval=10_000, config_id=3),
+    "ising_L8_h4_m1": dict(model=0, L=8, windows=4, walkers=1, overlap=0.75,
+                           lnf_final=1e-6, flatness=0.8, interval=10_000, config_id=1),
+}
+METRIC = "WL flip attempts/s"
+UNIT = "attempts/s"
+# Algorithmic integer work of one WL attempt (Philox4x32-10 call, site and neighbour index
+# arithmetic, energy change, window test, accept test, ln g / H update), in thread
+# instructions; the issue roofline is SMs x 128 lanes x SM clock.
+ALG_INSTR_PER_ATTEMPT = 85
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+THROTTLE_BITS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+                 0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown", 0x1: "gpu_idle",
+                 0x2: "applications_clocks_setting", 0x100: "display_clock_setting"}
+
+
+def seed_for(config_id: int, instance: int = 0) -> int:
+    return 0x5EED201400000000 + config_id * 1000 + instance
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def _oracle_worker(args):
+    wl, inst, rounds, warm = args
+    import oracle as O
+    o = O.REWL(wl["model"], wl["L"], wl["windows"], wl["overlap"], wl["walkers"], wl["lnf_final"],
+               wl["flatness"], seed=seed_for(wl["config_id"], inst), instance=inst,
+               interval=wl["interval"])
+    assert o.init() == 0
+    if warm:
+        o.run(warm)
+    t0 = time.perf_counter()
+    o.run(rounds)
+    return time.perf_counter() - t0
+
+
+def oracle_throughput(wl, procs: int, rounds: int, warm: int = 0):
+    """Independent oracle instances on `procs` host cores (spawned processes)."""
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        times = pool.map(_oracle_worker, [(wl, i, rounds, warm) for i in range(procs)])
+    attempts = procs * rounds * wl["windows"] * wl["walkers"] * wl["interval"]
+    return attempts / max(times), max(times), attempts
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index, self.proc, self.path = index, None, None
+
+    def __enter__(self):
+        try:
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,"
+                 "power.draw,clocks_event_reasons.active", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc or not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 4:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                bits = int(parts[3], 16)
+            except ValueError:
+                continue
+            for b, name in THROTTLE_BITS.items():
+                if bits & b and name != "gpu_idle":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- main arms
+def run_gpu(args, wl, rank, world):
+    import torch
+    import paper_1402_2328_gb300.rewl as R
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    r = R.REWL(wl["model"], wl["L"], wl["windows"], wl["overlap"], wl["walkers"], wl["lnf_final"],
+               wl["flatness"], seed=seed_for(wl["config_id"], rank), instance=rank,
+               interval=wl["interval"], stream=stream)
+    r.init()
+    per_round = r.nw * wl["interval"]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        r.step(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    r.set_param("profile", 1)
+    r.kernel_time(reset=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for a, b in evs:
+            flush.zero_()  # L2 flush, outside the timed events
+            a.record(stream)
+            r.step(1)
+            b.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = sum(a.elapsed_time(b) for a, b in evs)
+    move_ms, move_launches = r.kernel_time(reset=True)
+    r.set_param("profile", 0)
+    st = r.stats()
+    if st["exact_decisions"] < 0:
+        raise RuntimeError("bad stats")
+    # e2e through the blocking public call, reading window ln g back each round
+    lng_bytes = r.h * r.W * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.run(max_rounds=1)
+        _ = r.get_state("lng_mean")
+    e2e_s = time.perf_counter() - t0
+    t_max = step_ms
+    if world > 1:
+        t = torch.tensor([step_ms, e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max, e2e_s = float(t[0]), float(t[1])
+    attempts = per_round * args.steps * world
+    value = attempts / (t_max / 1e3)
+    # roofline of the move kernel (ALU/issue bound)
+    peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tinst = sms * 128 * sm_max_mhz * 1e6 / 1e12
+    move_avg_s = (move_ms / max(move_launches, 1)) / 1e3
+    achieved = ALG_INSTR_PER_ATTEMPT * per_round / move_avg_s / 1e12
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "model": "ising" if wl["model"] == 0 else f"potts{wl['model']}",
+                   "L": wl["L"], "windows": wl["windows"], "walkers_per_window": wl["walkers"],
+                   "walkers": r.nw, "interval": wl["interval"], "overlap": wl["overlap"],
+                   "flatness": wl["flatness"], "lnf_final": wl["lnf_final"],
+                   "attempts_per_step": per_round * world,
+                   "parallelism": f"replicas{world}" if world > 1 else "1gpu",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
+                     "frac": achieved / peak_tinst, "traffic": None,
+                     "kernel": "k_move", "kernel_ms_avg": move_avg_s * 1e3,
+                     "kernel_share_of_step": move_ms / step_ms if step_ms else None,
+                     "alg_inst_per_attempt": ALG_INSTR_PER_ATTEMPT,
+                     "peak_basis": f"{sms} SMs x 128 lanes x {sm_max_mhz:.0f} MHz (max SM clock)"},
+        "e2e": {"value": attempts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": lng_bytes + 48,
+                "call": "rewl_run(1 round) + rewl_get_state(lng_mean) per step"},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "exact_fraction": st["exact_decisions"] / max(st["attempts"], 1),
+    }
+    r.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ising_L64_h32_m16", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-rounds", type=int, default=2, help="oracle rounds per core (baseline)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    procs = os.cpu_count() or 1
+
+    if args.impl == "reference":
+        # the oracle is the reference arm: rank 0 only, host cores only
+        if rank != 0:
+            return
+        rounds = max(1, math.ceil(args.steps / procs))
+        val, tmax, attempts = oracle_throughput(wl, procs, rounds, warm=0)
+        out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": tmax * 1e3 / rounds, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
+               "config": {"workload": args.workload, "L": wl["L"], "windows": wl["windows"],
+                          "walkers_per_window": wl["walkers"], "interval": wl["interval"]},
+               "cpu_baseline": {"value": val, "unit": UNIT, "cores": procs, "kind": "oracle",
+                                "sample": f"{procs} independent oracle instances of the workload, "
+                                          f"{rounds} rounds each ({attempts:.3g} attempts)"},
+               "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # spawn the oracle pool before the first CUDA call
+        val, tmax, attempts = oracle_throughput(wl, procs, args.cpu_rounds)
+        cpu = {"value": val, "unit": UNIT, "cores": procs, "kind": "oracle",
+               "sample": f"{procs} independent single-threaded oracle instances of the workload, "
+                         f"{args.cpu_rounds} rounds each ({attempts:.3g} attempts, {tmax:.1f} s)"}
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_gpu(args, wl, rank, world)
+    if rank == 0:
+        if cpu is not None:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,246 @@
+/*
+ * rewl.h -- C ABI of the GB300 (sm_103a) replica-exchange Wang-Landau library.
+ *
+ * Method: Li, Vogel, Wuest, Landau, "A new paradigm for petascale Monte Carlo
+ * simulation: Replica exchange Wang-Landau sampling", arXiv:1402.2328.
+ *
+ * Conventions
+ *   - Every int-returning function returns REWL_OK (0) or a negative REWL_ERR_* code;
+ *     rewl_last_error() gives a message.  Nothing throws across this boundary.
+ *   - Host pointers ("host") are caller-owned and only read or written during the call.
+ *     Device pointers ("device") are caller-owned CUDA allocations on the current device;
+ *     the call only enqueues work on the given stream.
+ *   - A handle owns its device state (cudaMalloc'd in rewl_create, freed in rewl_destroy)
+ *     and enqueues all work on the stream given by rewl_set_stream (default: the legacy
+ *     default stream).  A handle is not thread safe.
+ *   - Models: model = 0 is the 2D Ising model E = -sum_<ij> s_i s_j (J = 1, s = +-1);
+ *     model = q >= 2 is the q-state Potts model E = -sum_<ij> delta(s_i, s_j).  L x L
+ *     square lattice with periodic boundaries, N = L*L sites, spins stored as int8.
+ *   - Energy bins: k counts unsatisfied bonds.  Ising: k = (E + 2N)/4 in [0, N] (B = N);
+ *     Potts: k = E + 2N in [0, 2N] (B = 2N).  ln g arrays over all bins have B+1 entries.
+ */
+#ifndef REWL_H
+#define REWL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define REWL_OK 0
+#define REWL_ERR_INVALID_ARG (-1)
+#define REWL_ERR_CUDA (-2)
+#define REWL_ERR_TIMEOUT (-3)
+#define REWL_ERR_NOT_CONVERGED (-4)
+#define REWL_ERR_BUFFER_TOO_SMALL (-5)
+#define REWL_ERR_PREP (-6)
+#define REWL_ERR_STATE (-7)
+#define REWL_ERR_IO (-8)
+
+/* rewl_run status */
+#define REWL_STATUS_RUNNING 0
+#define REWL_STATUS_DONE 1    /* every window reached ln f < ln f_final (Sec. 2, end)   */
+#define REWL_STATUS_BUDGET 2  /* max_rounds or max_seconds used up first                  */
+#define REWL_STATUS_ABORTED 3 /* rewl_abort() was called                                   */
+
+typedef struct rewl_s *rewl_t;
+
+/*
+ * rewl_create -- one REWL simulation (Sec. 2): the bin range [0, B] is split into `windows`
+ * equal-size windows with overlap fraction `overlap` (Fig. 1a); every window has
+ * `walkers_per_window` independent WL walkers with their own ln g(E) (float64) and H(E)
+ * (uint32).  The walk stops when every window reached ln f < lnf_final (f_final, Sec. 2);
+ * a walker's histogram is flat when min H >= flatness * mean H over the window's visited
+ * bins.  Window layout: o = 0.75 uses W = 4B/(h+3), lo_k = round(kB/(h+3)),
+ * hi_k = round((k+4)B/(h+3)), hi_{h-1} = B; other o use round(k s), round(k s + W) with
+ * W = B/(1+(h-1)(1-o)), s = (1-o) W.  Adjacent windows must overlap, else INVALID_ARG.
+ * Defaults: seed 0, ln f_init = 1, swap interval 10^4 moves, prep budget 100 sweeps.
+ * *out receives the handle.  Allocates device memory on the current device.
+ */
+int rewl_create(rewl_t *out, int model, int L, int windows, double overlap,
+                int walkers_per_window, double lnf_final, double flatness);
+
+/*
+ * rewl_set_param -- before rewl_init.  Keys: "lnf_init" (ln f of the first iteration,
+ * default 1), "interval" (WL moves per walker between two flatness checks and replica
+ * exchange attempts, Sec. 2; default 10000), "prep_budget" (sweeps allowed to bring a
+ * walker into its window, default 100), "instance" (0..2^24-1, enters the random
+ * stream, default 0), "graph_rounds" (rounds per CUDA-graph replay, default 32; 0 = no
+ * graph), "walkers_per_block" (warps per CTA of the move kernel; 0 = automatic),
+ * "check_all" (1 = decide every move with the float64 path as well and count
+ * disagreements; diagnostic), "profile" (1 = time move-kernel launches with CUDA events,
+ * see rewl_kernel_time; may be changed at any time).  Unknown key or bad value: INVALID_ARG.
+ */
+int rewl_set_param(rewl_t r, const char *key, double value);
+
+/* rewl_set_seed -- 64-bit seed; the Philox4x32-10 key is (seed low word, seed high word). */
+int rewl_set_seed(rewl_t r, uint64_t seed);
+
+/*
+ * rewl_set_lng_init -- warm start (host, n == B+1 float64 values): every walker of every
+ * window starts from lng_bins[lo..hi] instead of 0.  Before rewl_init.  Non-finite
+ * values inside any window: INVALID_ARG.
+ */
+int rewl_set_lng_init(rewl_t r, const double *lng_bins, int n);
+
+/*
+ * rewl_set_windows -- replace the window layout (host, 2*h ints lo[0..h-1], hi[0..h-1];
+ * lo[0] = 0, hi[h-1] = B, lo increasing, adjacent windows overlapping).  Before rewl_init.
+ * Used for run-time balanced splitting (Fig. 1b) and learned window boundaries.
+ */
+int rewl_set_windows(rewl_t r, const int *lo_hi, int h);
+
+/* rewl_set_stream -- cudaStream_t (as void*) for all later work of this handle. */
+int rewl_set_stream(rewl_t r, void *stream);
+
+/*
+ * rewl_init -- seeded random lattices (Ising +-1 / Potts 0..q-1 from Philox), then every
+ * walker is driven into its window: single-site moves accepted iff the distance of k to
+ * the window does not grow; after prep_budget sweeps a walker restarts from the ordered
+ * state.  REWL_ERR_PREP if a walker cannot reach its window.  Called by rewl_run if needed.
+ */
+int rewl_init(rewl_t r);
+
+/*
+ * rewl_run -- runs rounds until every window is finished, max_rounds rounds were done
+ * (max_rounds < 0: no limit) or max_seconds passed (<= 0: no limit).  One round is, for
+ * every walker, `interval` WL moves (accept iff ln u < ln g(E_old) - ln g(E_new), then
+ * ln g(E) += ln f, H(E)++; Sec. 2), then the per-walker flatness test and, for windows
+ * whose m walkers are all flat, the averaging of ln g over the m walkers, H = 0 and
+ * ln f /= 2 (Sec. 2), then replica exchange between windows (w, w+1), w = round mod 2,
+ * with acceptance min[1, g_i(E_X) g_j(E_Y) / (g_i(E_Y) g_j(E_X))] (Eq. 1).
+ * *status (may be NULL) gets a REWL_STATUS_* value.  Blocks until the work is done.
+ */
+int rewl_run(rewl_t r, double max_seconds, long long max_rounds, int *status);
+
+/* rewl_abort -- asks a running rewl_run (another thread) to stop after the current chunk. */
+int rewl_abort(rewl_t r);
+
+/*
+ * rewl_step -- enqueues `rounds` rounds (as rewl_run performs them) on the handle's stream
+ * and returns without waiting.  Rounds enqueued after every window finished do nothing.
+ * rewl_init must have succeeded.  Errors raised on the device show up in the next
+ * rewl_run / rewl_stats / rewl_get_state call.
+ */
+int rewl_step(rewl_t r, int rounds);
+
+/*
+ * rewl_kernel_time -- with parameter "profile" = 1, every move-kernel launch is bracketed
+ * by CUDA events on the handle's stream; this returns the summed duration (ms) and the
+ * number of timed launches since the last reset (waits for them), and resets if reset != 0.
+ */
+int rewl_kernel_time(rewl_t r, double *move_ms, long long *launches, int reset);
+
+/*
+ * rewl_get_lng -- ln g of one walker (walker >= 0) or the mean over the window's walkers
+ * (walker = -1, the mean of Sec. 2 taken in walker order) for bins lo..hi of `window`.
+ * out: host, cap >= hi-lo+1 float64; *lo, *hi (may be NULL) receive the window bounds.
+ */
+int rewl_get_lng(rewl_t r, int window, int walker, double *out, int cap, int *lo, int *hi);
+
+/*
+ * rewl_stitch -- joins the window means into one ln g over all B+1 bins (Sec. 3, Eq. 2):
+ * beta(k) = d ln g/dE by the 5-point stencil (3-point if no 5-point bin, Fig. 2); for each
+ * adjacent pair the join bin minimises |beta_w - beta_{w+1}| over the overlap (ties: the
+ * smaller bin, always after the previous join; no stencil: the bin valid in both windows
+ * nearest the overlap midpoint); window w+1 is shifted to agree at the join; bins below the
+ * join come from the left, the rest from the right.  Unvisited bins are -INFINITY.
+ * norm = 0: logsumexp = N ln q;  norm = 1: ln g(ground state) = ln q.
+ * out: host, cap >= B+1.  joins: host, h-1 ints, or NULL.  Runs on the GPU.
+ */
+int rewl_stitch(rewl_t r, double *out, int cap, int norm, int *joins);
+
+/*
+ * rewl_dims -- out (host, 8 ints): N, B, windows, walkers per window, W (row stride of
+ * per-walker ln g / H arrays = widest window), q, L, model.
+ */
+int rewl_dims(rewl_t r, int *out);
+
+/*
+ * rewl_get_state / rewl_set_state -- raw state, by field name, copied to/from host
+ * memory of exactly `bytes` bytes (BUFFER_TOO_SMALL otherwise).  Fields (nw = h*m):
+ *   "spins" int8[nw][N] (lattice carried by each walker slot), "k" int32[nw],
+ *   "lng" float64[nw][W], "H" uint32[nw][W], "step" uint64[nw] (WL attempts of the slot),
+ *   "acc" uint64[nw] (accepted moves), "flat" uint8[nw], "lnf" float64[h], "iter" int32[h],
+ *   "finished" uint8[h], "mask" uint8[h][W] (bins visited by the window), "swap_att"
+ *   uint64[h], "swap_acc" uint64[h] (pair (w,w+1) at index w), "pstep" uint64[nw],
+ *   "prep_restarts" int32[nw], "round" int64[1], "lo" int32[h], "hi" int32[h],
+ *   "n_exact" uint64[1] (moves decided by the float64 path), "n_mismatch" uint64[1],
+ *   "lng_mean" float64[h][W] (window means of ln g, walker order; computed on the GPU).
+ * rewl_set_state accepts "spins", "k", "lng", "H", "step" (tests plant states with it).
+ */
+int rewl_get_state(rewl_t r, const char *field, void *out, size_t bytes);
+int rewl_set_state(rewl_t r, const char *field, const void *in, size_t bytes);
+
+/* Run statistics (Sec. 2 exchange acceptance; Eq. 5 step counts). */
+typedef struct {
+    long long rounds;            /* rounds executed */
+    long long attempts;          /* WL attempts, all walkers */
+    long long accepted;          /* accepted WL moves */
+    long long swap_attempts;     /* replica-exchange attempts */
+    long long swap_accepted;     /* accepted exchanges */
+    long long exact_decisions;   /* moves decided by the float64 path */
+    long long prep_restarts;     /* walkers restarted from the ordered state */
+    int windows_finished;        /* windows with ln f < ln f_final */
+    int min_iteration;           /* smallest completed-iteration count over windows */
+    double max_lnf;              /* largest current ln f over windows */
+    double seconds;              /* wall time spent in rewl_run */
+} rewl_stats_t;
+int rewl_stats(rewl_t r, rewl_stats_t *out);
+
+/*
+ * rewl_checkpoint / rewl_restore -- the whole state (lattices, bins, ln g, H, step
+ * counters, flags, ln f, iterations, masks, round) to/from a binary file.  The random
+ * stream is a function of the step counters, so a restored run continues bit for bit.
+ * rewl_restore needs a handle created with the same parameters (else INVALID_ARG).
+ */
+int rewl_checkpoint(rewl_t r, const char *path);
+int rewl_restore(rewl_t r, const char *path);
+
+void rewl_destroy(rewl_t r);
+
+/* Message for the last error of r (or of a failed rewl_create / free function if r = NULL). */
+const char *rewl_last_error(rewl_t r);
+
+/*
+ * rewl_replay -- n independent WL attempt sequences of T steps each, on caller state, with
+ * caller-given random words instead of Philox (the move of Sec. 2 exactly as rewl_run
+ * performs it, same kernel).  All pointers are device pointers:
+ *   spins int8[n][N] (in/out), k int32[n] (in/out, must lie in [lo,hi]), lo/hi int32[n],
+ *   lng float64[n][W] (in/out, window-local: index k-lo), H uint32[n][W] (in/out),
+ *   lnf float64[n], frozen uint8[n] (1: no ln g/H update), words uint32[n][T][3]
+ *   (w0 -> site, w1 -> Potts new state, w2 -> u = (w2 + 1/2) 2^-32),
+ *   acc int32[n][T] and dk int32[n][T] (out: accepted flag and proposed bin change).
+ * W >= max(hi-lo+1); a case with k outside [lo, hi], |ln g| >= 2^30 or ln f outside
+ * (0, 2^20) makes the call fail with INVALID_ARG.  stream: cudaStream_t or NULL.
+ */
+int rewl_replay(int model, int L, int n, int W, int T, void *spins, void *k, const void *lo,
+                const void *hi, void *lng, void *H, const void *lnf, const void *frozen,
+                const void *words, void *acc, void *dk, void *stream);
+
+/*
+ * Diagnostics of the arithmetic the moves depend on (device pointers, stream or NULL):
+ *   rewl_philox: out[i][0..3] = Philox4x32-10(ctr[i][0..3], key[i][0..1]) for i < n
+ *     (Salmon et al., SC'11).
+ *   rewl_lnu: out[i] = the float64 ln((w[i] + 1/2) 2^-32) that decides moves and exchanges.
+ *   rewl_lnu_bound: over words w in [begin, end): max |screen(w) - lnu(w)| of the float32
+ *     screening value into max_err (device, 1 float64, overwritten), and the count of words
+ *     where the float64 value is >= 0 into n_bad (device, 1 uint64, overwritten).
+ *   rewl_lnu_eps: the screening tolerance the move kernel assumes (host value).
+ */
+int rewl_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n, void *stream);
+int rewl_lnu(const uint32_t *w, double *out, int n, void *stream);
+int rewl_lnu_bound(uint64_t begin, uint64_t end, double *max_err, unsigned long long *n_bad,
+                   void *stream);
+double rewl_lnu_eps(void);
+/* rewl_seqadd: out[i] = x[i] + f[i] + ... + f[i] (c[i] float64 additions, in order), device. */
+int rewl_seqadd(const double *x, const double *f, const uint32_t *c, double *out, int n,
+                void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REWL_H */

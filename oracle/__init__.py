@@ -127,7 +127,7 @@ class REWL:
 
     def __init__(self, model: int, L: int, windows: int, overlap: float, walkers: int,
                  lnf_final: float, flatness: float, seed: int, instance: int = 0,
-                 interval: int = 10_000, prep_budget: int = 1000, lnf_init: float = 1.0,
+                 interval: int = 10_000, prep_budget: int = 100, lnf_init: float = 1.0,
                  lng_init=None):
         self._lib = lib()
         self._h = self._lib.or_rewl_create(model, L, windows, overlap, walkers, lnf_final,

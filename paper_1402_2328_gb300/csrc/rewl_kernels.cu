@@ -1,0 +1,854 @@
+// rewl_kernels.cu -- the REWL hot path on sm_103a.
+//
+//   k_move        WL moves (Sec. 2): one warp per walker, lattice, ln g shadow and H in shared
+//                 memory; 32 proposals are drawn and evaluated in parallel, then resolved in
+//                 order (a proposal whose neighbourhood an earlier accepted flip touched is
+//                 re-evaluated), so the result equals the one-move-at-a-time walk exactly.
+//   k_check       per-walker flatness (warp-shuffle min / sum over visited bins) and window
+//                 advance: average ln g over the m walkers, H = 0, ln f /= 2 (Sec. 2).
+//   k_swap        replica exchange between windows (w, w+1), Eq. (1).
+//   k_init_prep   seeded lattices and the walk into the window.
+//   k_stitch      joining of Sec. 3, Eq. (2).
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "rewl_device.cuh"
+#include "rewl_kernels.cuh"
+
+namespace rewl {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__host__ __device__ inline int pad16(int n) { return (n + 15) & ~15; }
+__host__ __device__ inline int padw(int w) { return (w + 3) & ~3; }
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// Energy change (in bins) of a proposal at `site` on lattice sp, plus the new state.
+template <bool ISING>
+__device__ __forceinline__ int propose_dk(const int8_t *sp, const Lattice &lat, int q, int site,
+                                          int pr, int &snew)
+{
+    int l, r, u, d;
+    lat.nbrs(site, l, r, u, d);
+    const int s0 = sp[site];
+    const int a0 = sp[l], a1 = sp[r], a2 = sp[u], a3 = sp[d];
+    if (ISING) {
+        snew = -s0;
+        return (s0 * (a0 + a1 + a2 + a3)) / 2; // dE = 2 s0 sum, dk = dE / 4
+    } else {
+        int sn = s0 + 1 + pr;
+        if (sn >= q) sn -= q;
+        snew = sn;
+        return (int)(s0 == a0) + (int)(s0 == a1) + (int)(s0 == a2) + (int)(s0 == a3) -
+               (int)(sn == a0) - (int)(sn == a1) - (int)(sn == a2) - (int)(sn == a3);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// WL moves.  Decision rule (Sec. 2): accept iff ln u < ln g(k) - ln g(k'), where ln g are
+// the float64 values the sequential walk would hold at that moment.  In shared memory each
+// ln g(b) is shadowed by V(b) = round(ln g0(b) 2^32) + (visits so far) * round(ln f 2^32) as
+// int64; its distance to the float64 value is bounded (see shadow_tolerance), so comparing
+// V(k) - V(k') with the float32 screen of ln u decides all but a ~1e-5 fraction of moves;
+// those are decided from the float64 values, rebuilt exactly by seqadd from ln g0 and the
+// visit counts.  At the end the float64 ln g is rebuilt the same way for every bin.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ long long shadow_tolerance(double maxabs, int T, double lnf,
+                                                      bool frozen, double eps_l)
+{
+    const long long fb = __double_as_longlong(lnf);
+    const bool dyadic = (fb & 0x000fffffffffffffLL) == 0 && lnf >= 0x1p-32;
+    const double M = maxabs + (double)T * lnf; // |ln g| bound during the launch
+    const int ex = (int)((__double_as_longlong(M) >> 52) & 0x7ff);
+    const double ulpM = ex > 52 ? __longlong_as_double((long long)(ex - 52) << 52) : 0x1p-1022;
+    double ev; // |V 2^-32 - ln g| bound, in units of 2^-32
+    if (frozen)
+        ev = 0.5;
+    else if (dyadic) // additions exact except where a binade is crossed (< 64 times)
+        ev = 0.5 + 64.0 * ulpM * 0x1p32;
+    else // every addition may round; ln f 2^32 itself rounded
+        ev = 0.5 + 0.5 * (double)T + (double)T * ulpM * 0x1p31;
+    const double tq = 2.0 * ev + 2.0 + eps_l * 0x1p32 + 2.0;
+    return (long long)ceil(tq);
+}
+
+template <bool ISING, bool REPLAY>
+__global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int slot = blockIdx.x * c.walkers_per_block + wib;
+    if (slot >= s.nw) return;
+    if (s.status != nullptr && s.status->done) return;
+
+    const size_t per = move_smem_per_walker(s.N, s.W);
+    unsigned char *base = smem + (size_t)wib * per;
+    int8_t *sp = reinterpret_cast<int8_t *>(base);
+    long long *V = reinterpret_cast<long long *>(base + pad16(s.N));
+    uint32_t *Hs = reinterpret_cast<uint32_t *>(V + padw(s.W));
+
+    const int w = slot / s.m;
+    const int lo = s.lo[w], hi = s.hi[w], nb = hi - lo + 1;
+    int k = s.k[slot];
+    if (lo < 0 || nb < 1 || nb > s.W || k < lo || k > hi) { // malformed input: refuse
+        if (lane == 0) atomicOr(&s.status->err, ERR_INPUT);
+        return;
+    }
+    const double lnf = s.lnf[w];
+    const bool frozen = s.finished[w] != 0;
+    const int cfg = s.cfg ? s.cfg[slot] : slot;
+    int8_t *gsp = s.spins + (size_t)cfg * s.spin_stride;
+    double *glng = s.lng + (size_t)slot * s.W;
+    uint32_t *gH = s.H + (size_t)slot * s.W;
+    const Lattice lat{s.L, s.N, s.magic};
+    const int T = c.T;
+
+    // ---- load lattice, shadow ln g, H
+    if (s.vec_spins) {
+        const int4 *src = reinterpret_cast<const int4 *>(gsp);
+        int4 *dst = reinterpret_cast<int4 *>(sp);
+        for (int i = lane; i < (s.N >> 4); i += 32) dst[i] = src[i];
+    } else {
+        for (int i = lane; i < s.N; i += 32) sp[i] = gsp[i];
+    }
+    double mx = 0.0;
+    bool bad = false;
+    for (int b = lane; b < nb; b += 32) {
+        const double x = glng[b];
+        bad = bad || !(fabs(x) < 0x1p30); // also catches NaN
+        mx = fmax(mx, fabs(x));
+        V[b] = bad ? 0LL : __double2ll_rn(__dmul_rn(x, 0x1p32));
+        Hs[b] = gH[b];
+    }
+    mx = warp_max(mx);
+    if (__any_sync(FULL, bad) || !(lnf > 0.0 && lnf < 0x1p20)) {
+        // the int64 shadow would overflow: leave the state untouched
+        if (lane == 0) atomicOr(&s.status->err, ERR_RANGE);
+        return;
+    }
+    const long long lnfq = __double2ll_rn(__dmul_rn(lnf, 0x1p32));
+    const long long Tq = shadow_tolerance(mx, T, lnf, frozen, c.eps_l);
+    __syncwarp();
+
+    long long Vk = V[k - lo];
+    const unsigned long long st0 = s.step[slot];
+    unsigned int nacc = 0, nex = 0, nmis = 0;
+    const uint32_t tag = (s.inst << 8) | TAG_MOVE;
+
+    for (int base_t = 0; base_t < T; base_t += 32) {
+        const int n = min(32, T - base_t);
+        // ---- parallel phase: lane j evaluates proposal base_t + j on the current lattice
+        uint32_t w0, w1, w2;
+        if (REPLAY) {
+            if (lane < n) {
+                const uint32_t *wp = c.words + ((size_t)slot * T + base_t + lane) * 3;
+                w0 = wp[0];
+                w1 = wp[1];
+                w2 = wp[2];
+            } else {
+                w0 = w1 = w2 = 0u;
+            }
+        } else {
+            const unsigned long long st = st0 + (unsigned long long)(base_t + lane);
+            const u32x4 r = philox((uint32_t)st, (uint32_t)(st >> 32), (uint32_t)slot, tag,
+                                   s.key0, s.key1);
+            w0 = r.x;
+            w1 = r.y;
+            w2 = r.z;
+        }
+        const int site = (int)mulhi(w0, (uint32_t)s.N);
+        int nl, nr, nu, nd;
+        lat.nbrs(site, nl, nr, nu, nd);
+        const int pr = ISING ? 0 : (int)mulhi(w1, (uint32_t)(s.q - 1));
+        int snew;
+        const int dk = propose_dk<ISING>(sp, lat, s.q, site, pr, snew);
+        const long long lq = __float2ll_rn(lnu32(w2) * 0x1p32f);
+        const long long thr_acc = lq + Tq, thr_rej = lq - Tq;
+        bool dirty = false;
+
+        // ---- serial phase: resolve the proposals in order (warp-uniform)
+        for (int i = 0; i < n; ++i) {
+            int dki = __shfl_sync(FULL, dk, i);
+            const int sitei = __shfl_sync(FULL, site, i);
+            int snewi = __shfl_sync(FULL, snew, i);
+            const unsigned dmask = __ballot_sync(FULL, dirty);
+            if ((dmask >> i) & 1u) { // neighbourhood changed by an earlier flip of this batch
+                __syncwarp();
+                const int pri = __shfl_sync(FULL, pr, i);
+                dki = propose_dk<ISING>(sp, lat, s.q, sitei, pri, snewi);
+            }
+            const int kp = k + dki;
+            bool acc;
+            if (dki == 0) {
+                acc = true; // ln g(k) - ln g(k) = 0 >= 0
+            } else if (kp < lo || kp > hi) {
+                acc = false; // outside the window
+            } else {
+                const long long Vkp = V[kp - lo];
+                const long long dq = Vk - Vkp;
+                const long long ta = __shfl_sync(FULL, thr_acc, i);
+                const long long tr = __shfl_sync(FULL, thr_rej, i);
+                int screen = dq > ta ? 1 : (dq < tr ? 0 : -1);
+                if (screen < 0 || c.check_all) {
+                    __syncwarp();
+                    const uint32_t w2i = __shfl_sync(FULL, w2, i);
+                    const double lk = seqadd(glng[k - lo], lnf, Hs[k - lo] - gH[k - lo]);
+                    const double lkp = seqadd(glng[kp - lo], lnf, Hs[kp - lo] - gH[kp - lo]);
+                    const double d = __dsub_rn(lk, lkp);
+                    const bool ex = (d >= 0.0) || (lnu64(w2i) < d);
+                    if (screen >= 0 && (int)ex != screen) ++nmis;
+                    if (screen < 0) ++nex;
+                    screen = ex ? 1 : 0;
+                }
+                acc = screen == 1;
+                if (acc) Vk = Vkp;
+            }
+            if (acc) {
+                sp[sitei] = (int8_t)snewi; // every lane stores the same byte
+                k = kp;
+                ++nacc;
+                dirty = dirty || ((lane > i) && (site == sitei || nl == sitei || nr == sitei ||
+                                                 nu == sitei || nd == sitei));
+            }
+            if (!frozen) {
+                Vk += lnfq;
+                V[k - lo] = Vk; // every lane stores the same value
+                if (lane == 0) Hs[k - lo] += 1u;
+            }
+            if (REPLAY && lane == 0) {
+                c.acc_out[(size_t)slot * T + base_t + i] = acc ? 1 : 0;
+                c.dk_out[(size_t)slot * T + base_t + i] = dki;
+            }
+        }
+        __syncwarp();
+    }
+
+    // ---- write back lattice, float64 ln g (rebuilt exactly), H, counters
+    if (s.vec_spins) {
+        const int4 *src = reinterpret_cast<const int4 *>(sp);
+        int4 *dst = reinterpret_cast<int4 *>(gsp);
+        for (int i = lane; i < (s.N >> 4); i += 32) dst[i] = src[i];
+    } else {
+        for (int i = lane; i < s.N; i += 32) gsp[i] = sp[i];
+    }
+    if (!frozen) {
+        for (int b = lane; b < nb; b += 32) {
+            const uint32_t h1 = Hs[b], h0 = gH[b];
+            if (h1 != h0) {
+                glng[b] = seqadd(glng[b], lnf, h1 - h0);
+                gH[b] = h1;
+            }
+        }
+    }
+    if (lane == 0) {
+        s.k[slot] = k;
+        s.step[slot] = st0 + (unsigned long long)T;
+        s.acc[slot] += nacc;
+        if (nex) atomicAdd(&s.status->n_exact, (unsigned long long)nex);
+        if (nmis) atomicAdd(&s.status->n_mismatch, (unsigned long long)nmis);
+    }
+}
+
+cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st)
+{
+    const int G = c.walkers_per_block;
+    const size_t smem = (size_t)G * move_smem_per_walker(s.N, s.W);
+    const dim3 grid((s.nw + G - 1) / G), block(32 * G);
+    const bool ising = s.model == 0;
+    cudaError_t e;
+#define REWL_LAUNCH_MOVE(I, R)                                                                   \
+    do {                                                                                         \
+        e = cudaFuncSetAttribute(k_move<I, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                 (int)smem);                                                     \
+        if (e != cudaSuccess) return e;                                                          \
+        k_move<I, R><<<grid, block, smem, st>>>(s, c);                                           \
+    } while (0)
+    if (ising) {
+        if (c.words) REWL_LAUNCH_MOVE(true, true);
+        else REWL_LAUNCH_MOVE(true, false);
+    } else {
+        if (c.words) REWL_LAUNCH_MOVE(false, true);
+        else REWL_LAUNCH_MOVE(false, false);
+    }
+#undef REWL_LAUNCH_MOVE
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Seeded lattices and prep into the window (one thread per walker; runs once).
+// ---------------------------------------------------------------------------------------
+__device__ int bin_of_lattice(const int8_t *sp, int L, int N, bool ising)
+{
+    long long E = 0;
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            const int a = sp[y * L + x];
+            const int r = sp[y * L + (x + 1 == L ? 0 : x + 1)];
+            const int d = sp[(y + 1 == L ? 0 : y + 1) * L + x];
+            if (ising) E -= (long long)(a * r + a * d);
+            else E -= (long long)((a == r) + (a == d));
+        }
+    return ising ? (int)((E + 2LL * N) / 4) : (int)(E + 2LL * N);
+}
+
+__device__ __forceinline__ int dist_to(int k, int lo, int hi)
+{
+    return k < lo ? lo - k : (k > hi ? k - hi : 0);
+}
+
+__global__ void k_init_prep(State s, long long prep_budget)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= s.nw) return;
+    const bool ising = s.model == 0;
+    const int w = slot / s.m, lo = s.lo[w], hi = s.hi[w], N = s.N;
+    int8_t *sp = s.spins + (size_t)slot * s.spin_stride; // cfg[slot] == slot at start
+    const Lattice lat{s.L, N, s.magic};
+    for (int c = 0; 4 * c < N; ++c) {
+        const u32x4 r = philox((uint32_t)c, 0u, (uint32_t)slot, (s.inst << 8) | TAG_INIT,
+                               s.key0, s.key1);
+        const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+        for (int j = 0; j < 4 && 4 * c + j < N; ++j)
+            sp[4 * c + j] = ising ? (int8_t)((wv[j] >> 31) ? -1 : 1)
+                                  : (int8_t)mulhi(wv[j], (uint32_t)s.q);
+    }
+    int k = bin_of_lattice(sp, s.L, N, ising);
+    unsigned long long ps = 0;
+    const unsigned long long budget = (unsigned long long)prep_budget * (unsigned long long)N;
+    int restarts = 0;
+    for (int phase = 0; phase < 2 && dist_to(k, lo, hi) > 0; ++phase) {
+        if (phase == 1) {
+            for (int j = 0; j < N; ++j) sp[j] = ising ? 1 : 0;
+            k = 0;
+            ++restarts;
+        }
+        const unsigned long long end = ps + budget;
+        while (dist_to(k, lo, hi) > 0 && ps < end) {
+            const u32x4 r = philox((uint32_t)ps, (uint32_t)(ps >> 32), (uint32_t)slot,
+                                   (s.inst << 8) | TAG_PREP, s.key0, s.key1);
+            const int site = (int)mulhi(r.x, (uint32_t)N);
+            int snew, dk;
+            if (ising) dk = propose_dk<true>(sp, lat, s.q, site, 0, snew);
+            else dk = propose_dk<false>(sp, lat, s.q, site, (int)mulhi(r.y, (uint32_t)(s.q - 1)), snew);
+            if (dist_to(k + dk, lo, hi) <= dist_to(k, lo, hi)) {
+                sp[site] = (int8_t)snew;
+                k += dk;
+            }
+            ++ps;
+        }
+    }
+    s.k[slot] = k;
+    s.cfg[slot] = slot;
+    s.pstep[slot] = ps;
+    s.restarts[slot] = restarts;
+    if (dist_to(k, lo, hi) > 0) atomicOr(&s.status->err, ERR_PREP);
+}
+
+cudaError_t launch_init_prep(const State &s, long long prep_budget, cudaStream_t st)
+{
+    k_init_prep<<<(s.nw + 63) / 64, 64, 0, st>>>(s, prep_budget);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Flatness + window advance (Sec. 2).  One CTA per window.
+// ---------------------------------------------------------------------------------------
+__global__ void k_check(State s, double flatness, double lnf_final)
+{
+    const int w = blockIdx.x;
+    if (s.status->done || s.finished[w]) return;
+    const int m = s.m, W = s.W, nb = s.hi[w] - s.lo[w] + 1;
+    uint8_t *mask = s.mask + (size_t)w * W;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        uint8_t v = mask[b];
+        for (int i = 0; i < m && !v; ++i) v = s.H[(size_t)(w * m + i) * W + b] > 0u;
+        mask[b] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int i = wid; i < m; i += nwarp) {
+        const int g = w * m + i;
+        if (s.flat[g]) continue;
+        const uint32_t *H = s.H + (size_t)g * W;
+        unsigned long long sum = 0;
+        uint32_t mn = 0xffffffffu;
+        int cnt = 0;
+        for (int b = lane; b < nb; b += 32)
+            if (mask[b]) {
+                const uint32_t v = H[b];
+                sum += v;
+                mn = min(mn, v);
+                ++cnt;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sum += __shfl_xor_sync(FULL, sum, o);
+            mn = min(mn, __shfl_xor_sync(FULL, mn, o));
+            cnt += __shfl_xor_sync(FULL, cnt, o);
+        }
+        if (lane == 0 && cnt > 0 &&
+            __dmul_rn((double)mn, (double)cnt) >= __dmul_rn(flatness, (double)sum))
+            s.flat[g] = 1;
+    }
+    __syncthreads();
+    __shared__ int all;
+    if (threadIdx.x == 0) {
+        int a = 1;
+        for (int i = 0; i < m; ++i) a &= s.flat[w * m + i];
+        all = a;
+    }
+    __syncthreads();
+    if (!all) return;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < m; ++i) acc = __dadd_rn(acc, s.lng[(size_t)(w * m + i) * W + b]);
+        const double avg = __ddiv_rn(acc, (double)m);
+        for (int i = 0; i < m; ++i) {
+            s.lng[(size_t)(w * m + i) * W + b] = avg;
+            s.H[(size_t)(w * m + i) * W + b] = 0u;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < m; ++i) s.flat[w * m + i] = 0;
+        const double nl = __dmul_rn(s.lnf[w], 0.5);
+        s.lnf[w] = nl;
+        s.iter[w] += 1;
+        if (nl < lnf_final) s.finished[w] = 1;
+    }
+}
+
+cudaError_t launch_check(const State &s, double flatness, double lnf_final, cudaStream_t st)
+{
+    k_check<<<s.h, 256, 0, st>>>(s, flatness, lnf_final);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Replica exchange (Eq. 1) between windows (w, w+1), w = round mod 2.  One warp per pair;
+// lane 0 draws the partner permutation and the decisions (m is small), the swap itself
+// exchanges configuration indices and bins.
+// ---------------------------------------------------------------------------------------
+__global__ void k_swap(State s)
+{
+    if (s.status->done) return;
+    const long long rd = s.status->round;
+    const int w = 2 * blockIdx.x + (int)(rd & 1);
+    if (w + 1 >= s.h || threadIdx.x != 0) return;
+    const int m = s.m, W = s.W;
+    __shared__ int perm[MAX_M];
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    const uint32_t tag = (s.inst << 8) | TAG_SWAP;
+    for (int i = m - 1; i >= 1; --i) {
+        const u32x4 r = philox((uint32_t)i, (uint32_t)rd, (uint32_t)w, tag, s.key0, s.key1);
+        const int j = (int)mulhi(r.x, (uint32_t)(i + 1));
+        const int t = perm[i];
+        perm[i] = perm[j];
+        perm[j] = t;
+    }
+    const int loA = s.lo[w], hiA = s.hi[w], loB = s.lo[w + 1], hiB = s.hi[w + 1];
+    unsigned long long att = 0, acc = 0;
+    for (int i = 0; i < m; ++i) {
+        const int a = w * m + i, b = (w + 1) * m + perm[i];
+        const int kx = s.k[a], ky = s.k[b];
+        ++att;
+        if (kx < loB || kx > hiB || ky < loA || ky > hiA) continue;
+        const double *ga = s.lng + (size_t)a * W, *gb = s.lng + (size_t)b * W;
+        const double lnP = __dadd_rn(__dsub_rn(ga[kx - loA], ga[ky - loA]),
+                                     __dsub_rn(gb[ky - loB], gb[kx - loB]));
+        bool ok = lnP >= 0.0;
+        if (!ok) {
+            const u32x4 r = philox((uint32_t)(m + i), (uint32_t)rd, (uint32_t)w, tag, s.key0,
+                                   s.key1);
+            ok = lnu64(r.x) < lnP;
+        }
+        if (ok) {
+            const int t = s.cfg[a];
+            s.cfg[a] = s.cfg[b];
+            s.cfg[b] = t;
+            s.k[a] = ky;
+            s.k[b] = kx;
+            ++acc;
+        }
+    }
+    s.swap_att[w] += att;
+    s.swap_acc[w] += acc;
+}
+
+cudaError_t launch_swap(const State &s, cudaStream_t st)
+{
+    if (s.h < 2) return cudaSuccess;
+    k_swap<<<(s.h + 1) / 2, 32, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+__global__ void k_round_end(State s)
+{
+    if (s.status->done) return;
+    s.status->round += 1;
+    int all = 1;
+    for (int w = 0; w < s.h; ++w) all &= s.finished[w];
+    if (all) s.status->done = 1;
+}
+
+cudaError_t launch_round_end(const State &s, cudaStream_t st)
+{
+    k_round_end<<<1, 1, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+__global__ void k_set_done(State s)
+{
+    int all = 1;
+    for (int w = 0; w < s.h; ++w) all &= s.finished[w];
+    s.status->done = all;
+}
+
+cudaError_t launch_set_done(const State &s, cudaStream_t st)
+{
+    k_set_done<<<1, 1, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Joining (Sec. 3, Eq. 2).
+// ---------------------------------------------------------------------------------------
+__global__ void k_window_mean(State s, double *out)
+{
+    const int w = blockIdx.x, nb = s.hi[w] - s.lo[w] + 1;
+    for (int b = threadIdx.x; b < s.W; b += blockDim.x) {
+        double v = 0.0;
+        if (b < nb) {
+            double acc = 0.0;
+            for (int i = 0; i < s.m; ++i) acc = __dadd_rn(acc, s.lng[(size_t)(w * s.m + i) * s.W + b]);
+            v = __ddiv_rn(acc, (double)s.m);
+        }
+        out[(size_t)w * s.W + b] = v;
+    }
+}
+
+cudaError_t launch_window_mean(const State &s, double *out, cudaStream_t st)
+{
+    k_window_mean<<<s.h, 256, 0, st>>>(s, out);
+    return cudaGetLastError();
+}
+
+// beta by the 5-point (npts 5) or 3-point stencil at window-local bin b; 0 if not defined.
+__device__ int stencil_beta(const double *l, const uint8_t *v, int nb, int b, int step, int npts,
+                            double de, double *beta)
+{
+    if (npts == 5) {
+        if (b - 2 * step < 0 || b + 2 * step >= nb) return 0;
+        if (!(v[b - 2 * step] && v[b - step] && v[b + step] && v[b + 2 * step])) return 0;
+        const double num = __dadd_rn(
+            __dsub_rn(__dadd_rn(-l[b + 2 * step], __dmul_rn(8.0, l[b + step])),
+                      __dmul_rn(8.0, l[b - step])),
+            l[b - 2 * step]);
+        *beta = __ddiv_rn(num, __dmul_rn(__dmul_rn(12.0, de), (double)step));
+        return 1;
+    }
+    if (b - step < 0 || b + step >= nb) return 0;
+    if (!(v[b - step] && v[b + step])) return 0;
+    *beta = __ddiv_rn(__dsub_rn(l[b + step], l[b - step]),
+                      __dmul_rn(__dmul_rn(2.0, de), (double)step));
+    return 1;
+}
+
+// Block-wide argmin of (value, key): smaller value, ties -> smaller key.
+__device__ void block_argmin(double &v, int &key)
+{
+    __shared__ double sv[32];
+    __shared__ int sk[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(FULL, v, o);
+        const int ok = __shfl_xor_sync(FULL, key, o);
+        if (ov < v || (ov == v && ok < key)) {
+            v = ov;
+            key = ok;
+        }
+    }
+    if (lane == 0) {
+        sv[wid] = v;
+        sk[wid] = key;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        v = lane < nw ? sv[lane] : INFINITY;
+        key = lane < nw ? sk[lane] : 0x7fffffff;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(FULL, v, o);
+            const int ok = __shfl_xor_sync(FULL, key, o);
+            if (ov < v || (ov == v && ok < key)) {
+                v = ov;
+                key = ok;
+            }
+        }
+        if (lane == 0) {
+            sv[0] = v;
+            sk[0] = key;
+        }
+    }
+    __syncthreads();
+    v = sv[0];
+    key = sk[0];
+    __syncthreads();
+}
+
+__device__ double block_reduce_max(double v)
+{
+    __shared__ double sv[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_max(v);
+    if (lane == 0) sv[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sv[lane] : -INFINITY;
+        v = warp_max(v);
+        if (lane == 0) sv[0] = v;
+    }
+    __syncthreads();
+    v = sv[0];
+    __syncthreads();
+    return v;
+}
+
+__device__ double block_reduce_sum(double v)
+{
+    __shared__ double sv[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0) sv[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sv[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        if (lane == 0) sv[0] = v;
+    }
+    __syncthreads();
+    v = sv[0];
+    __syncthreads();
+    return v;
+}
+
+// One CTA: joins are found pair by pair (each depends on the previous one); the stencils
+// and the argmin over the overlap are block-parallel.
+__global__ void k_stitch(State s, const double *mean, double de, int step, int norm, double target,
+                         double *out, int *joins, int *ok, int B)
+{
+    const int W = s.W;
+    __shared__ double shift_s;
+    __shared__ int prev_s, fail_s;
+    for (int b = threadIdx.x; b <= B; b += blockDim.x) out[b] = -INFINITY;
+    __syncthreads();
+    {
+        const int lo0 = s.lo[0], hi0 = s.hi[0];
+        for (int b = lo0 + (int)threadIdx.x; b <= hi0; b += blockDim.x)
+            if (s.mask[b - lo0]) out[b] = mean[b - lo0];
+    }
+    if (threadIdx.x == 0) {
+        shift_s = 0.0;
+        prev_s = -1;
+        fail_s = 0;
+    }
+    __syncthreads();
+    for (int w = 0; w + 1 < s.h; ++w) {
+        const double *la = mean + (size_t)w * W, *lb = mean + (size_t)(w + 1) * W;
+        const uint8_t *va = s.mask + (size_t)w * W, *vb = s.mask + (size_t)(w + 1) * W;
+        const int loa = s.lo[w], hia = s.hi[w], lob = s.lo[w + 1], hib = s.hi[w + 1];
+        const int nba = hia - loa + 1, nbb = hib - lob + 1;
+        const int prev = prev_s;
+        int kj = -1;
+        for (int npts = 5; npts >= 3 && kj < 0; npts -= 2) {
+            double best = INFINITY;
+            int bk = 0x7fffffff;
+            for (int k = lob + (int)threadIdx.x; k <= hia; k += blockDim.x) {
+                if (k <= prev || !va[k - loa] || !vb[k - lob]) continue;
+                double ba, bb;
+                if (!stencil_beta(la, va, nba, k - loa, step, npts, de, &ba)) continue;
+                if (!stencil_beta(lb, vb, nbb, k - lob, step, npts, de, &bb)) continue;
+                const double db = fabs(__dsub_rn(ba, bb));
+                if (db < best || (db == best && k < bk)) {
+                    best = db;
+                    bk = k;
+                }
+            }
+            block_argmin(best, bk);
+            if (best < INFINITY) kj = bk;
+        }
+        if (kj < 0) { // nearest bin valid in both to the overlap midpoint, ties -> smaller
+            const int mid2 = lob + hia;
+            double bd = INFINITY;
+            int bk = 0x7fffffff;
+            for (int k = lob + (int)threadIdx.x; k <= hia; k += blockDim.x) {
+                if (k <= prev || !va[k - loa] || !vb[k - lob]) continue;
+                const double d = fabs((double)(2 * k - mid2));
+                if (d < bd || (d == bd && k < bk)) {
+                    bd = d;
+                    bk = k;
+                }
+            }
+            block_argmin(bd, bk);
+            if (bd < INFINITY) kj = bk;
+        }
+        if (kj < 0) {
+            if (threadIdx.x == 0) fail_s = 1;
+            break;
+        }
+        if (threadIdx.x == 0) {
+            shift_s = __dsub_rn(__dadd_rn(la[kj - loa], shift_s), lb[kj - lob]);
+            joins[w] = kj;
+            prev_s = kj;
+        }
+        __syncthreads();
+        const double sh = shift_s;
+        for (int b = max(kj, lob) + (int)threadIdx.x; b <= hib; b += blockDim.x)
+            out[b] = vb[b - lob] ? __dadd_rn(lb[b - lob], sh) : -INFINITY;
+        __syncthreads();
+    }
+    __syncthreads();
+    if (fail_s) {
+        if (threadIdx.x == 0) *ok = 0;
+        return;
+    }
+    if (norm == 0) {
+        double mx = -INFINITY;
+        for (int b = threadIdx.x; b <= B; b += blockDim.x) mx = fmax(mx, out[b]);
+        mx = block_reduce_max(mx);
+        double sum = 0.0;
+        for (int b = threadIdx.x; b <= B; b += blockDim.x)
+            if (out[b] > -INFINITY) sum += exp(out[b] - mx);
+        sum = block_reduce_sum(sum);
+        const double cst = (mx + log(sum)) - target;
+        for (int b = threadIdx.x; b <= B; b += blockDim.x)
+            if (out[b] > -INFINITY) out[b] -= cst;
+    } else {
+        int b0 = 0x7fffffff;
+        double dummy = 0.0;
+        for (int b = threadIdx.x; b <= B; b += blockDim.x)
+            if (out[b] > -INFINITY && b < b0) b0 = b;
+        block_argmin(dummy, b0);
+        if (b0 > B) {
+            if (threadIdx.x == 0) *ok = 0;
+            return;
+        }
+        const double cst = __dsub_rn(out[b0], target);
+        __syncthreads();
+        for (int b = threadIdx.x; b <= B; b += blockDim.x)
+            if (out[b] > -INFINITY) out[b] = __dsub_rn(out[b], cst);
+    }
+    if (threadIdx.x == 0) *ok = 1;
+}
+
+cudaError_t launch_stitch(const State &s, const double *mean, double de, int step, int norm,
+                          double target, double *out, int *joins, int *ok, int B, cudaStream_t st)
+{
+    k_stitch<<<1, 256, 0, st>>>(s, mean, de, step, norm, target, out, joins, ok, B);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Diagnostics.
+// ---------------------------------------------------------------------------------------
+__global__ void k_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const u32x4 r = philox(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3],
+                           key[2 * i], key[2 * i + 1]);
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n,
+                          cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_philox<<<(n + 255) / 256, 256, 0, st>>>(ctr, key, out, n);
+    return cudaGetLastError();
+}
+
+__global__ void k_lnu(const uint32_t *w, double *out, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = lnu64(w[i]);
+}
+
+cudaError_t launch_lnu(const uint32_t *w, double *out, int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_lnu<<<(n + 255) / 256, 256, 0, st>>>(w, out, n);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ void atomic_max_pos(double *addr, double v)
+{
+    // non-negative doubles order like their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_lnu_bound(uint64_t begin, uint64_t end, double *max_err, unsigned long long *n_bad)
+{
+    double mx = 0.0;
+    unsigned long long bad = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = begin + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < end; x += stride) {
+        const uint32_t w = (uint32_t)x;
+        const double e = lnu64(w);
+        const double f = (double)lnu32(w);
+        mx = fmax(mx, fabs(f - e));
+        bad += (e >= 0.0);
+    }
+    mx = warp_max(mx);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(FULL, bad, o);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(max_err, mx);
+        if (bad) atomicAdd(n_bad, bad);
+    }
+}
+
+cudaError_t launch_lnu_bound(uint64_t begin, uint64_t end, double *max_err,
+                             unsigned long long *n_bad, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(max_err, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(n_bad, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    if (end <= begin) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_lnu_bound<<<sms * 8, 256, 0, st>>>(begin, end, max_err, n_bad);
+    return cudaGetLastError();
+}
+
+__global__ void k_seqadd(const double *x, const double *f, const uint32_t *c, double *out, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = seqadd(x[i], f[i], c[i]);
+}
+
+cudaError_t launch_seqadd(const double *x, const double *f, const uint32_t *c, double *out,
+                          int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_seqadd<<<(n + 127) / 128, 128, 0, st>>>(x, f, c, out, n);
+    return cudaGetLastError();
+}
+
+} // namespace rewl

@@ -1,0 +1,80 @@
+// rewl_kernels.cuh -- kernel argument blocks and launchers shared by the host runtime.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rewl {
+
+// Device-side run status (one per handle).
+struct DevStatus {
+    long long round;              // rounds completed
+    int done;                     // every window finished
+    int err;                      // ERR_* bits
+    unsigned long long n_exact;   // moves decided by the float64 path
+    unsigned long long n_mismatch;// check_all: screen decisions that disagreed (must stay 0)
+};
+enum : int { ERR_PREP = 1, ERR_RANGE = 2, ERR_INPUT = 4 };
+constexpr int MAX_M = 1024; // walkers per window (exchange permutation in shared memory)
+constexpr size_t MAX_SMEM_PER_CTA = 227u * 1024u;
+
+// Per-walker-slot state of one REWL instance, all device pointers.
+struct State {
+    int model, q, L, N, nw, m, h, W, spin_stride;
+    int vec_spins;            // lattices 16-byte aligned with N % 16 == 0: int4 copies
+    uint32_t magic;           // ceil(2^32 / L)
+    int8_t *spins;            // [nw][spin_stride] lattices (owned by configuration index)
+    int *cfg;                 // [nw] slot -> configuration index
+    int *k;                   // [nw] current bin of the slot's configuration
+    double *lng;              // [nw][W] window-local ln g
+    uint32_t *H;              // [nw][W]
+    unsigned long long *step; // [nw]
+    unsigned long long *acc;  // [nw]
+    unsigned long long *pstep;// [nw]
+    int *restarts;            // [nw]
+    uint8_t *flat;            // [nw]
+    const int *lo, *hi;       // [h]
+    double *lnf;              // [h]
+    int *iter;                // [h]
+    uint8_t *finished;        // [h]
+    uint8_t *mask;            // [h][W]
+    unsigned long long *swap_att, *swap_acc; // [h]
+    DevStatus *status;
+    uint32_t key0, key1, inst;
+};
+
+struct MoveCfg {
+    int T;                  // attempts per walker in this launch
+    int walkers_per_block;  // warps per CTA
+    int check_all;
+    double eps_l;
+    const uint32_t *words;  // replay: [nw][T][3], else nullptr (Philox)
+    int *acc_out, *dk_out;  // replay: [nw][T]
+};
+
+// Shared memory of one walker in the move kernel: lattice (16-byte padded), int64 ln g
+// shadow and uint32 H over the window (padded to 4 bins).
+__host__ __device__ inline size_t move_smem_per_walker(int N, int W)
+{
+    return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 12u;
+}
+cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st);
+cudaError_t launch_init_prep(const State &s, long long prep_budget, cudaStream_t st);
+cudaError_t launch_check(const State &s, double flatness, double lnf_final, cudaStream_t st);
+cudaError_t launch_swap(const State &s, cudaStream_t st);
+cudaError_t launch_round_end(const State &s, cudaStream_t st);
+cudaError_t launch_set_done(const State &s, cudaStream_t st);
+cudaError_t launch_window_mean(const State &s, double *out /*[h][W]*/, cudaStream_t st);
+cudaError_t launch_stitch(const State &s, const double *mean, double de, int step, int norm,
+                          double target, double *out /*B+1*/, int *joins /*h-1*/,
+                          int *ok /*1*/, int B, cudaStream_t st);
+
+cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n,
+                          cudaStream_t st);
+cudaError_t launch_lnu(const uint32_t *w, double *out, int n, cudaStream_t st);
+cudaError_t launch_lnu_bound(uint64_t begin, uint64_t end, double *max_err,
+                             unsigned long long *n_bad, cudaStream_t st);
+cudaError_t launch_seqadd(const double *x, const double *f, const uint32_t *c, double *out,
+                          int n, cudaStream_t st);
+
+} // namespace rewl

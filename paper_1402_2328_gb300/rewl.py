@@ -1,0 +1,274 @@
+"""ctypes binding of librewl.so (include/rewl.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module converts numpy
+arrays / torch CUDA tensors to pointers and error codes to exceptions.  If the library
+is not built, ``lib()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librewl.so")
+_lib = None
+
+STATUS = {0: "running", 1: "done", 2: "budget", 3: "aborted"}
+
+
+class REWLError(RuntimeError):
+    pass
+
+
+class _Stats(C.Structure):
+    _fields_ = [("rounds", C.c_longlong), ("attempts", C.c_longlong), ("accepted", C.c_longlong),
+                ("swap_attempts", C.c_longlong), ("swap_accepted", C.c_longlong),
+                ("exact_decisions", C.c_longlong), ("prep_restarts", C.c_longlong),
+                ("windows_finished", C.c_int), ("min_iteration", C.c_int),
+                ("max_lnf", C.c_double), ("seconds", C.c_double)]
+
+
+def lib():
+    """The loaded CUDA library; raises if it was not built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise REWLError(f"CUDA library not built ({LIB_PATH}); run "
+                            "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        P, I, D = C.c_void_p, C.c_int, C.c_double
+        sig = {
+            "rewl_create": ([P, I, I, I, D, I, D, D], I),
+            "rewl_set_param": ([P, C.c_char_p, D], I),
+            "rewl_set_seed": ([P, C.c_uint64], I),
+            "rewl_set_lng_init": ([P, P, I], I),
+            "rewl_set_windows": ([P, P, I], I),
+            "rewl_set_stream": ([P, P], I),
+            "rewl_init": ([P], I),
+            "rewl_run": ([P, D, C.c_longlong, P], I),
+            "rewl_abort": ([P], I),
+            "rewl_step": ([P, I], I),
+            "rewl_kernel_time": ([P, P, P, I], I),
+            "rewl_get_lng": ([P, I, I, P, I, P, P], I),
+            "rewl_stitch": ([P, P, I, I, P], I),
+            "rewl_dims": ([P, P], I),
+            "rewl_get_state": ([P, C.c_char_p, P, C.c_size_t], I),
+            "rewl_set_state": ([P, C.c_char_p, P, C.c_size_t], I),
+            "rewl_stats": ([P, P], I),
+            "rewl_checkpoint": ([P, C.c_char_p], I),
+            "rewl_restore": ([P, C.c_char_p], I),
+            "rewl_destroy": ([P], None),
+            "rewl_last_error": ([P], C.c_char_p),
+            "rewl_replay": ([I, I, I, I, I] + [P] * 12, I),
+            "rewl_philox": ([P, P, P, I, P], I),
+            "rewl_lnu": ([P, P, I, P], I),
+            "rewl_lnu_bound": ([C.c_uint64, C.c_uint64, P, P, P], I),
+            "rewl_lnu_eps": ([], D),
+            "rewl_seqadd": ([P, P, P, P, I, P], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return [n for n in dir(lib()) if n.startswith("rewl_")]
+
+
+def _check(rc, handle=None):
+    if rc != 0:
+        msg = lib().rewl_last_error(handle)
+        raise REWLError(f"rewl error {rc}: {msg.decode() if msg else ''}")
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or a torch tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+_FIELDS = {
+    "spins": (np.int8, "nwN"), "k": (np.int32, "nw"), "lng": (np.float64, "nwW"),
+    "H": (np.uint32, "nwW"), "step": (np.uint64, "nw"), "acc": (np.uint64, "nw"),
+    "flat": (np.uint8, "nw"), "lnf": (np.float64, "h"), "iter": (np.int32, "h"),
+    "finished": (np.uint8, "h"), "mask": (np.uint8, "hW"), "swap_att": (np.uint64, "h"),
+    "swap_acc": (np.uint64, "h"), "pstep": (np.uint64, "nw"), "prep_restarts": (np.int32, "nw"),
+    "round": (np.int64, "1"), "lo": (np.int32, "h"), "hi": (np.int32, "h"),
+    "n_exact": (np.uint64, "1"), "n_mismatch": (np.uint64, "1"), "lng_mean": (np.float64, "hW"),
+}
+
+
+class REWL:
+    """One REWL simulation on the current CUDA device (see include/rewl.h)."""
+
+    def __init__(self, model: int, L: int, windows: int, overlap: float, walkers: int,
+                 lnf_final: float, flatness: float, seed: int = 0, stream=None, **params):
+        self._lib = lib()
+        h = C.c_void_p()
+        _check(self._lib.rewl_create(C.byref(h), model, L, windows, overlap, walkers,
+                                     lnf_final, flatness))
+        self._h = h
+        self._update_dims()
+        self.set_seed(seed)
+        for key, v in params.items():
+            self.set_param(key, v)
+        self.set_stream(stream)
+
+    def _update_dims(self):
+        d = np.zeros(8, np.int32)
+        _check(self._lib.rewl_dims(self._h, _ptr(d)), self._h)
+        self.N, self.B, self.h, self.m, self.W, self.q, self.L, self.model = (int(v) for v in d)
+        self.nw = self.h * self.m
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rewl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- configuration
+    def set_param(self, key: str, value: float):
+        _check(self._lib.rewl_set_param(self._h, key.encode(), float(value)), self._h)
+
+    def set_seed(self, seed: int):
+        _check(self._lib.rewl_set_seed(self._h, int(seed) & (2 ** 64 - 1)), self._h)
+
+    def set_lng_init(self, lng_bins):
+        a = np.ascontiguousarray(lng_bins, np.float64)
+        _check(self._lib.rewl_set_lng_init(self._h, _ptr(a), len(a)), self._h)
+
+    def set_windows(self, lo, hi):
+        a = np.ascontiguousarray(np.concatenate([lo, hi]), np.int32)
+        _check(self._lib.rewl_set_windows(self._h, _ptr(a), len(lo)), self._h)
+        self._update_dims()
+
+    def set_stream(self, stream=None):
+        _check(self._lib.rewl_set_stream(self._h, _stream_ptr(stream)), self._h)
+
+    # ---- running
+    def init(self):
+        _check(self._lib.rewl_init(self._h), self._h)
+
+    def run(self, max_seconds: float = 0.0, max_rounds: int = -1) -> str:
+        st = C.c_int(0)
+        _check(self._lib.rewl_run(self._h, float(max_seconds), int(max_rounds), C.byref(st)),
+               self._h)
+        return STATUS[st.value]
+
+    def abort(self):
+        _check(self._lib.rewl_abort(self._h), self._h)
+
+    def step(self, rounds: int = 1):
+        """Enqueue rounds on the handle's stream without waiting."""
+        _check(self._lib.rewl_step(self._h, int(rounds)), self._h)
+
+    def kernel_time(self, reset: bool = True):
+        ms, n = C.c_double(), C.c_longlong()
+        _check(self._lib.rewl_kernel_time(self._h, C.byref(ms), C.byref(n), int(reset)), self._h)
+        return ms.value, n.value
+
+    # ---- results
+    def get_lng(self, window: int, walker: int = -1):
+        out = np.zeros(self.W, np.float64)
+        lo, hi = C.c_int(), C.c_int()
+        _check(self._lib.rewl_get_lng(self._h, window, walker, _ptr(out), len(out),
+                                      C.byref(lo), C.byref(hi)), self._h)
+        return out[: hi.value - lo.value + 1], lo.value, hi.value
+
+    def stitch(self, norm: int = 0):
+        out = np.zeros(self.B + 1, np.float64)
+        joins = np.zeros(max(self.h - 1, 1), np.int32)
+        _check(self._lib.rewl_stitch(self._h, _ptr(out), len(out), norm, _ptr(joins)), self._h)
+        return out, joins[: self.h - 1]
+
+    def _shape(self, code):
+        return {"nwN": (self.nw, self.N), "nw": (self.nw,), "nwW": (self.nw, self.W),
+                "h": (self.h,), "hW": (self.h, self.W), "1": (1,)}[code]
+
+    def get_state(self, field: str) -> np.ndarray:
+        dt, code = _FIELDS[field]
+        out = np.zeros(self._shape(code), dt)
+        _check(self._lib.rewl_get_state(self._h, field.encode(), _ptr(out), out.nbytes), self._h)
+        return out
+
+    def state(self) -> dict:
+        s = {f: self.get_state(f) for f in _FIELDS}
+        s["round"] = int(s["round"][0])
+        return s
+
+    def set_state(self, field: str, value):
+        dt, code = _FIELDS[field]
+        a = np.ascontiguousarray(value, dt).reshape(self._shape(code))
+        _check(self._lib.rewl_set_state(self._h, field.encode(), _ptr(a), a.nbytes), self._h)
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(self._lib.rewl_stats(self._h, C.byref(s)), self._h)
+        return {n: getattr(s, n) for n, _ in _Stats._fields_}
+
+    def checkpoint(self, path: str):
+        _check(self._lib.rewl_checkpoint(self._h, os.fsencode(path)), self._h)
+
+    def restore(self, path: str):
+        _check(self._lib.rewl_restore(self._h, os.fsencode(path)), self._h)
+
+
+# ---- free functions (device tensors in, device tensors out)
+def replay(model, L, spins, k, lo, hi, lng, H, lnf, frozen, words, acc, dk, stream=None):
+    """In-place replay through the move kernel; all arguments are CUDA tensors."""
+    n, T = words.shape[0], words.shape[1]
+    W = lng.shape[1]
+    _check(lib().rewl_replay(model, L, n, W, T, _ptr(spins), _ptr(k), _ptr(lo), _ptr(hi),
+                             _ptr(lng), _ptr(H), _ptr(lnf), _ptr(frozen), _ptr(words), _ptr(acc),
+                             _ptr(dk), _stream_ptr(stream)))
+
+
+def philox(ctr, key, out, stream=None):
+    _check(lib().rewl_philox(_ptr(ctr), _ptr(key), _ptr(out), ctr.shape[0], _stream_ptr(stream)))
+
+
+def lnu(words, out, stream=None):
+    _check(lib().rewl_lnu(_ptr(words), _ptr(out), words.numel(), _stream_ptr(stream)))
+
+
+def lnu_bound(begin, end, max_err, n_bad, stream=None):
+    _check(lib().rewl_lnu_bound(int(begin), int(end), _ptr(max_err), _ptr(n_bad),
+                                _stream_ptr(stream)))
+
+
+def lnu_eps() -> float:
+    return float(lib().rewl_lnu_eps())
+
+
+def seqadd(x, f, c, out, stream=None):
+    _check(lib().rewl_seqadd(_ptr(x), _ptr(f), _ptr(c), _ptr(out), x.numel(), _stream_ptr(stream)))

@@ -1,0 +1,64 @@
+"""CPU-only checks of the boundary: the library builds, loads and exports every symbol
+that include/rewl.h declares; the binding fails loudly without it.  No compute calls."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(rewl_\w+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1402_2328_gb300 import build as B
+    return B.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["rewl_create", "rewl_run", "rewl_get_lng", "rewl_stitch", "rewl_replay",
+              "rewl_set_param", "rewl_set_lng_init", "rewl_set_stream", "rewl_stats",
+              "rewl_checkpoint", "rewl_restore", "rewl_destroy", "rewl_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = ctypes.CDLL(built)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header(built):
+    import paper_1402_2328_gb300.rewl as R
+    lib = R.lib()
+    for n in _declared():
+        assert getattr(lib, n).argtypes is not None or n == "rewl_lnu_eps", n
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    import paper_1402_2328_gb300.rewl as R
+    monkeypatch.setattr(R, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(R, "_lib", None)
+    with pytest.raises(R.REWLError):
+        R.lib()
+
+
+def test_oracle_is_not_imported_by_the_product():
+    pkg = os.path.join(ROOT, "paper_1402_2328_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
+                assert "rewl_oracle" not in src and "librewl_oracle" not in src, f
