@@ -144,7 +144,8 @@ def run_gpu(args, wl, rank, world):
     sms = props.multi_processor_count
     r = R.REWL(wl["model"], wl["L"], wl["windows"], wl["overlap"], wl["walkers"], wl["lnf_final"],
                wl["flatness"], seed=seed_for(wl["config_id"], rank), instance=rank,
-               interval=wl["interval"], stream=stream)
+               interval=wl["interval"], stream=stream,
+               lnf_init=args.lnf_init)
     r.init()
     per_round = r.nw * wl["interval"]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -203,6 +204,7 @@ def run_gpu(args, wl, rank, world):
                    "L": wl["L"], "windows": wl["windows"], "walkers_per_window": wl["walkers"],
                    "walkers": r.nw, "interval": wl["interval"], "overlap": wl["overlap"],
                    "flatness": wl["flatness"], "lnf_final": wl["lnf_final"],
+                   "lnf_init": args.lnf_init,
                    "attempts_per_step": per_round * world,
                    "parallelism": f"replicas{world}" if world > 1 else "1gpu",
                    "l2": "flushed (256 MB write) before every timed step"},
@@ -232,6 +234,7 @@ def main():
     ap.add_argument("--workload", default="ising_L64_h32_m16", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-rounds", type=int, default=2, help="oracle rounds per core (baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lnf-init", type=float, default=1.0, help="ln f of the first iteration")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -218,7 +218,7 @@ int rewl_create(rewl_t *out, int model, int L, int windows, double overlap, int 
         return REWL_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (L < 2 || L > 4096 || (model != 0 && (model < 2 || model > 127)) || windows < 1 ||
+    if (L < 2 || L > 255 || (model != 0 && (model < 2 || model > 127)) || windows < 1 ||
         walkers_per_window < 1 || walkers_per_window > MAX_M || !(lnf_final > 0.0) ||
         !(flatness >= 0.0) || (long long)windows * walkers_per_window > (1LL << 24)) {
         g_err = "rewl_create: invalid argument";
@@ -262,7 +262,7 @@ int rewl_set_param(rewl_t r, const char *key, double v)
     }
     if (r->inited) return r->fail(REWL_ERR_STATE, "rewl_set_param after rewl_init");
     if (k == "lnf_init" && v > 0.0 && std::isfinite(v)) r->lnf_init = v;
-    else if (k == "interval" && v >= 1 && v <= 1e9) r->interval = (long long)v;
+    else if (k == "interval" && v >= 1 && v <= 1e8) r->interval = (long long)v;
     else if (k == "prep_budget" && v >= 1 && v <= 1e9) r->prep_budget = (long long)v;
     else if (k == "instance" && v >= 0 && v < 16777216.0) r->inst = (uint32_t)v;
     else if (k == "graph_rounds" && v >= 0 && v <= 4096) r->graph_rounds = (int)v;
@@ -858,7 +858,7 @@ int rewl_replay(int model, int L, int n, int W, int T, void *spins, void *k, con
                 const void *hi, void *lng, void *H, const void *lnf, const void *frozen,
                 const void *words, void *acc, void *dk, void *stream)
 {
-    if (n < 0 || L < 2 || L > 4096 || W < 1 || T < 1 || (model != 0 && (model < 2 || model > 127)) ||
+    if (n < 0 || L < 2 || L > 255 || W < 1 || T < 1 || T > 100000000 || (model != 0 && (model < 2 || model > 127)) ||
         !spins || !k || !lo || !hi || !lng || !H || !lnf || !frozen || !words || !acc || !dk) {
         g_err = "rewl_replay: invalid argument";
         return REWL_ERR_INVALID_ARG;

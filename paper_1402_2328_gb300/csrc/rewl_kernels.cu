@@ -52,34 +52,73 @@ __device__ __forceinline__ int propose_dk(const int8_t *sp, const Lattice &lat, 
 }
 
 // ---------------------------------------------------------------------------------------
-// WL moves.  Decision rule (Sec. 2): accept iff ln u < ln g(k) - ln g(k'), where ln g are
-// the float64 values the sequential walk would hold at that moment.  In shared memory each
-// ln g(b) is shadowed by V(b) = round(ln g0(b) 2^32) + (visits so far) * round(ln f 2^32) as
-// int64; its distance to the float64 value is bounded (see shadow_tolerance), so comparing
-// V(k) - V(k') with the float32 screen of ln u decides all but a ~1e-5 fraction of moves;
-// those are decided from the float64 values, rebuilt exactly by seqadd from ln g0 and the
-// visit counts.  At the end the float64 ln g is rebuilt the same way for every bin.
+// WL moves.  Decision rule (Sec. 2): accept iff ln u < ln g(k) - ln g(k'), with the float64
+// ln g the one-move-at-a-time walk would hold at that moment.
+//
+// One warp per walker.  Shared memory holds the lattice (int8), an int64 shadow
+// V(b) = round(ln g0(b) 2^32) + (visits) * round(ln f 2^32) of ln g over the window, H, and one
+// claim stamp per site.  Moves are taken in batches of up to 32:
+//   1. lane j draws the proposal of step t+j (Philox) and evaluates its energy change on the
+//      lattice as it was at the batch start; the batch is limited to its conflict-free prefix
+//      (no proposal sits on the site or a neighbour of an earlier one), so those energy
+//      changes stay exact whatever earlier steps of the batch do;
+//   2. lane j holds, as float32 relative to the bin k0 where the batch started, ln g of bin
+//      k0-16+j (+inf outside the window);
+//   3. the warp walks the steps in order computing only the path: one shuffle fetches
+//      ln g(k'), and the move is accepted/rejected in float32 when ln u is farther than a
+//      proven error bound from ln g(k) - ln g(k'); a step inside the bound or whose k' leaves
+//      the cached bins is flagged, the batch is cut there, and that one step is decided from
+//      the float64 values rebuilt exactly (seqadd of the interval-start ln g and the visit
+//      counts);
+//   4. the side effects of the steps done (spin flips, visits of V and H) are applied
+//      lane-parallel.
+// At the end of the launch the float64 ln g of every bin is rebuilt exactly from its visit
+// count, so the state equals that of the sequential walk bit for bit.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ long long shadow_tolerance(double maxabs, int T, double lnf,
-                                                      bool frozen, double eps_l)
+__device__ __forceinline__ double shadow_error(double maxabs, int T, double lnf, bool frozen)
 {
+    // bound on |V(b) 2^-32 - ln g(b)| in units of 2^-32 over a launch of T moves
     const long long fb = __double_as_longlong(lnf);
     const bool dyadic = (fb & 0x000fffffffffffffLL) == 0 && lnf >= 0x1p-32;
-    const double M = maxabs + (double)T * lnf; // |ln g| bound during the launch
+    const double M = maxabs + (double)T * lnf;
     const int ex = (int)((__double_as_longlong(M) >> 52) & 0x7ff);
     const double ulpM = ex > 52 ? __longlong_as_double((long long)(ex - 52) << 52) : 0x1p-1022;
-    double ev; // |V 2^-32 - ln g| bound, in units of 2^-32
-    if (frozen)
-        ev = 0.5;
-    else if (dyadic) // additions exact except where a binade is crossed (< 64 times)
-        ev = 0.5 + 64.0 * ulpM * 0x1p32;
-    else // every addition may round; ln f 2^32 itself rounded
-        ev = 0.5 + 0.5 * (double)T + (double)T * ulpM * 0x1p31;
-    const double tq = 2.0 * ev + 2.0 + eps_l * 0x1p32 + 2.0;
-    return (long long)ceil(tq);
+    if (frozen) return 0.5;
+    if (dyadic) return 0.5 + 64.0 * ulpM * 0x1p32; // exact additions except binade crossings
+    return 0.5 + 0.5 * (double)T + (double)T * ulpM * 0x1p31; // every addition may round
 }
 
-template <bool ISING, bool REPLAY>
+__device__ __forceinline__ float ulpf(float x)
+{
+    // unit in the last place of |x| (x normal), as a power of two
+    const int e = (__float_as_int(fabsf(x)) >> 23) & 0xff;
+    return e > 23 ? __int_as_float((e - 23) << 23) : 0x1p-126f;
+}
+
+__device__ __forceinline__ float warp_maxf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// Float64 decision from the exact values (rare).  All lanes take part.
+__device__ __noinline__ bool exact_decision(const double *glng, const uint32_t *gH,
+                                            const uint32_t *Hs, int lo, int k, int kp, int k0,
+                                            int cnt, double lnf, bool frozen, uint32_t w2)
+{
+    const int ck = __shfl_sync(FULL, cnt, (k - k0 + 16) & 31);
+    const int ckp = __shfl_sync(FULL, cnt, (kp - k0 + 16) & 31);
+    __syncwarp();
+    const uint32_t vk = frozen ? 0u : Hs[k - lo] - gH[k - lo] + (uint32_t)ck;
+    const uint32_t vkp = frozen ? 0u : Hs[kp - lo] - gH[kp - lo] + (uint32_t)ckp;
+    const double lk = seqadd(glng[k - lo], lnf, vk);
+    const double lkp = seqadd(glng[kp - lo], lnf, vkp);
+    const double d = __dsub_rn(lk, lkp);
+    return (d >= 0.0) || (lnu64(w2) < d);
+}
+
+template <bool ISING, bool REPLAY, bool CHECK>
 __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -93,6 +132,7 @@ __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
     int8_t *sp = reinterpret_cast<int8_t *>(base);
     long long *V = reinterpret_cast<long long *>(base + pad16(s.N));
     uint32_t *Hs = reinterpret_cast<uint32_t *>(V + padw(s.W));
+    unsigned *stamp = reinterpret_cast<unsigned *>(Hs + padw(s.W)); // [N] batch claims
 
     const int w = slot / s.m;
     const int lo = s.lo[w], hi = s.hi[w], nb = hi - lo + 1;
@@ -105,12 +145,12 @@ __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
     const bool frozen = s.finished[w] != 0;
     const int cfg = s.cfg ? s.cfg[slot] : slot;
     int8_t *gsp = s.spins + (size_t)cfg * s.spin_stride;
-    double *glng = s.lng + (size_t)slot * s.W;
+    const double *glng = s.lng + (size_t)slot * s.W;
     uint32_t *gH = s.H + (size_t)slot * s.W;
     const Lattice lat{s.L, s.N, s.magic};
     const int T = c.T;
 
-    // ---- load lattice, shadow ln g, H
+    // ---- load lattice, shadow ln g, H; clear the claim stamps
     if (s.vec_spins) {
         const int4 *src = reinterpret_cast<const int4 *>(gsp);
         int4 *dst = reinterpret_cast<int4 *>(sp);
@@ -118,6 +158,7 @@ __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
     } else {
         for (int i = lane; i < s.N; i += 32) sp[i] = gsp[i];
     }
+    for (int i = lane; i < s.N; i += 32) stamp[i] = 0u;
     double mx = 0.0;
     bool bad = false;
     for (int b = lane; b < nb; b += 32) {
@@ -128,27 +169,46 @@ __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
         Hs[b] = gH[b];
     }
     mx = warp_max(mx);
-    if (__any_sync(FULL, bad) || !(lnf > 0.0 && lnf < 0x1p20)) {
-        // the int64 shadow would overflow: leave the state untouched
+    if (__any_sync(FULL, bad) || !(lnf >= 0x1p-32 && lnf < 0x1p20)) {
+        // the int64 shadow would overflow or lose the increment: leave the state untouched
         if (lane == 0) atomicOr(&s.status->err, ERR_RANGE);
         return;
     }
     const long long lnfq = __double2ll_rn(__dmul_rn(lnf, 0x1p32));
-    const long long Tq = shadow_tolerance(mx, T, lnf, frozen, c.eps_l);
+    // interval-constant part of the float32 screening margin (ln units)
+    const float Mbase = (float)(c.eps_l + 2.0 * shadow_error(mx, T, lnf, frozen) * 0x1p-32) + 0x1p-21f;
+    const float lnf_f = frozen ? 0.0f : (float)lnf;
+    constexpr int REACH = ISING ? 13 : 11; // cache holds k0-16..k0+15; |dk| <= 2 (Ising), 4 (Potts)
+    const int span = hi - lo;
     __syncwarp();
 
-    long long Vk = V[k - lo];
     const unsigned long long st0 = s.step[slot];
     unsigned int nacc = 0, nex = 0, nmis = 0;
     const uint32_t tag = (s.inst << 8) | TAG_MOVE;
 
-    for (int base_t = 0; base_t < T; base_t += 32) {
-        const int n = min(32, T - base_t);
-        // ---- parallel phase: lane j evaluates proposal base_t + j on the current lattice
+    int t = 0;
+    unsigned batch = 0;
+    while (t < T) {
+        ++batch;
+        const int n = min(32, T - t);
+        // ---- register cache of ln g around k0 (float32, relative to bin k0)
+        const int k0 = k, base = k0 - 16;
+        const int bj = base + lane;
+        const bool bin_ok = bj >= lo && bj <= hi;
+        float Lw = 0.0f;
+        if (bin_ok) {
+            const long long x = V[bj - lo] - V[k0 - lo];
+            Lw = __fmaf_rn(__uint2float_rn((uint32_t)x), 0x1p-32f, (float)(int)(x >> 32));
+        }
+        const float Mx = warp_maxf(bin_ok ? fabsf(Lw) : 0.0f) + 33.0f * lnf_f + 0x1p-20f;
+        const float M = Mbase + 40.0f * ulpf(2.0f * Mx);
+        if (!bin_ok) Lw = INFINITY; // a move there is rejected: ln g(k) - inf < ln u
+
+        // ---- parallel phase: lane j evaluates proposal t + j on the batch-start lattice
         uint32_t w0, w1, w2;
         if (REPLAY) {
             if (lane < n) {
-                const uint32_t *wp = c.words + ((size_t)slot * T + base_t + lane) * 3;
+                const uint32_t *wp = c.words + ((size_t)slot * T + t + lane) * 3;
                 w0 = wp[0];
                 w1 = wp[1];
                 w2 = wp[2];
@@ -156,8 +216,8 @@ __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
                 w0 = w1 = w2 = 0u;
             }
         } else {
-            const unsigned long long st = st0 + (unsigned long long)(base_t + lane);
-            const u32x4 r = philox((uint32_t)st, (uint32_t)(st >> 32), (uint32_t)slot, tag,
+            const unsigned long long sn = st0 + (unsigned long long)(t + lane);
+            const u32x4 r = philox((uint32_t)sn, (uint32_t)(sn >> 32), (uint32_t)slot, tag,
                                    s.key0, s.key1);
             w0 = r.x;
             w1 = r.y;
@@ -169,65 +229,125 @@ __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
         const int pr = ISING ? 0 : (int)mulhi(w1, (uint32_t)(s.q - 1));
         int snew;
         const int dk = propose_dk<ISING>(sp, lat, s.q, site, pr, snew);
-        const long long lq = __float2ll_rn(lnu32(w2) * 0x1p32f);
-        const long long thr_acc = lq + Tq, thr_rej = lq - Tq;
-        bool dirty = false;
-
-        // ---- serial phase: resolve the proposals in order (warp-uniform)
-        for (int i = 0; i < n; ++i) {
-            int dki = __shfl_sync(FULL, dk, i);
-            const int sitei = __shfl_sync(FULL, site, i);
-            int snewi = __shfl_sync(FULL, snew, i);
-            const unsigned dmask = __ballot_sync(FULL, dirty);
-            if ((dmask >> i) & 1u) { // neighbourhood changed by an earlier flip of this batch
-                __syncwarp();
-                const int pri = __shfl_sync(FULL, pr, i);
-                dki = propose_dk<ISING>(sp, lat, s.q, sitei, pri, snewi);
-            }
-            const int kp = k + dki;
-            bool acc;
-            if (dki == 0) {
-                acc = true; // ln g(k) - ln g(k) = 0 >= 0
-            } else if (kp < lo || kp > hi) {
-                acc = false; // outside the window
-            } else {
-                const long long Vkp = V[kp - lo];
-                const long long dq = Vk - Vkp;
-                const long long ta = __shfl_sync(FULL, thr_acc, i);
-                const long long tr = __shfl_sync(FULL, thr_rej, i);
-                int screen = dq > ta ? 1 : (dq < tr ? 0 : -1);
-                if (screen < 0 || c.check_all) {
-                    __syncwarp();
-                    const uint32_t w2i = __shfl_sync(FULL, w2, i);
-                    const double lk = seqadd(glng[k - lo], lnf, Hs[k - lo] - gH[k - lo]);
-                    const double lkp = seqadd(glng[kp - lo], lnf, Hs[kp - lo] - gH[kp - lo]);
-                    const double d = __dsub_rn(lk, lkp);
-                    const bool ex = (d >= 0.0) || (lnu64(w2i) < d);
-                    if (screen >= 0 && (int)ex != screen) ++nmis;
-                    if (screen < 0) ++nex;
-                    screen = ex ? 1 : 0;
-                }
-                acc = screen == 1;
-                if (acc) Vk = Vkp;
-            }
-            if (acc) {
-                sp[sitei] = (int8_t)snewi; // every lane stores the same byte
-                k = kp;
-                ++nacc;
-                dirty = dirty || ((lane > i) && (site == sitei || nl == sitei || nr == sitei ||
-                                                 nu == sitei || nd == sitei));
-            }
-            if (!frozen) {
-                Vk += lnfq;
-                V[k - lo] = Vk; // every lane stores the same value
-                if (lane == 0) Hs[k - lo] += 1u;
-            }
-            if (REPLAY && lane == 0) {
-                c.acc_out[(size_t)slot * T + base_t + i] = acc ? 1 : 0;
-                c.dk_out[(size_t)slot * T + base_t + i] = dki;
+        const float thr = lnu32(w2);
+        // conflict-free prefix: proposal j may be resolved on the batch-start lattice only if
+        // no earlier proposal of the batch sits on its site or a neighbour
+        const unsigned claim = (batch << 5) | (unsigned)(31 - lane);
+        if (lane < n) atomicMax(&stamp[site], claim);
+        __syncwarp();
+        bool conflict = false;
+        {
+            const int xs[5] = {site, nl, nr, nu, nd};
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                const unsigned v = stamp[xs[m]];
+                conflict = conflict || ((v >> 5) == batch && (31 - (int)(v & 31u)) < lane);
             }
         }
+        const unsigned cmask = __ballot_sync(FULL, conflict && lane < n);
+        const int J = cmask ? (__ffs(cmask) - 1) : n; // >= 1: lane 0 never conflicts
+
+        // ---- serial phase: the path k_0, k_1, ... only.  Every step runs unconditionally;
+        // a step that is too close to call in float32 or whose k' leaves the cache is only
+        // flagged, and the batch is cut at the first flagged step afterwards (the steps after
+        // it are discarded), so no bookkeeping sits on the dependency chain.
+        const float thrA = thr + M; // sure accept: thr + M < d
+        const float thrR = thr - M; // sure reject: thr - M > d
+        int kc = k;
+        float Lk = 0.0f;
+        unsigned accbits = 0u, badbits = 0u, saccbits = 0u, srejbits = 0u;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if ((i & 7) == 0 && i > 0 && (badbits != 0u || i >= J)) break;
+            const int dki = __shfl_sync(FULL, dk, i);
+            const float tA = __shfl_sync(FULL, thrA, i);
+            const float tR = __shfl_sync(FULL, thrR, i);
+            const int kp = kc + dki;
+            const int xo = kp - base;
+            const float Lkp = __shfl_sync(FULL, Lw, xo & 31);
+            const float d = Lk - Lkp;
+            const bool dz = dki == 0;
+            const bool a0 = tA < d;
+            const bool act = dz || a0;
+            // CHECK: every in-window move is also decided by the float64 path, and the float32
+            // verdict is kept to count disagreements
+            const bool unsure = CHECK ? (Lkp < INFINITY) : !(tR > d);
+            const bool bad = (unsigned)xo >= 32u || (!dz && (CHECK ? unsure : (!a0 && unsure)));
+            badbits |= bad ? (1u << i) : 0u;
+            if (CHECK) {
+                saccbits |= a0 ? (1u << i) : 0u;
+                srejbits |= (tR > d) ? (1u << i) : 0u;
+            }
+            const bool leave = act && !dz;
+            if (leave && lane == kc - base) Lw = Lk; // keep the running value of the bin left
+            kc = act ? kp : kc;
+            Lk = (leave ? Lkp : Lk) + lnf_f;
+            accbits |= act ? (1u << i) : 0u;
+        }
+        const unsigned stopbits = badbits | (J >= 32 ? 0u : (0xffffffffu << J));
+        const int ndone = stopbits ? __ffs(stopbits) - 1 : 32;
+        const bool amb_stop = ndone < J;
+        accbits &= ndone >= 32 ? 0xffffffffu : ((1u << ndone) - 1u);
+        // bin after each step: prefix sum of the accepted energy changes
+        int pos = ((accbits >> lane) & 1u) ? dk : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, pos, o);
+            if (lane >= o) pos += v;
+        }
+        const int mypos = k + pos;
+        kc = ndone > 0 ? k + __shfl_sync(FULL, pos, ndone - 1) : k;
+        // float32 verdict at the cut (CHECK): 1 sure accept, 0 sure reject, -1 unsure
+        const int scr = !CHECK || ndone >= 32 ? -1
+                        : (((saccbits >> ndone) & 1u) ? 1 : (((srejbits >> ndone) & 1u) ? 0 : -1));
+
+        // ---- side effects of steps 0..ndone-1
+        const bool mine = lane < ndone;
+        if (mine && ((accbits >> lane) & 1u)) sp[site] = (int8_t)snew; // conflict-free sites
+        if (mine && !frozen) {
+            atomicAdd(&Hs[mypos - lo], 1u);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&V[mypos - lo]),
+                      (unsigned long long)lnfq);
+        }
+        if (REPLAY && mine) {
+            c.acc_out[(size_t)slot * T + t + lane] = (accbits >> lane) & 1u;
+            c.dk_out[(size_t)slot * T + t + lane] = dk;
+        }
+        nacc += __popc(accbits);
+        k = kc;
+        t += ndone;
         __syncwarp();
+
+        // ---- a proposal too close to call in float32: decide it from the float64 values
+        if (amb_stop) {
+            const int i = ndone;
+            const int dki = __shfl_sync(FULL, dk, i);
+            const int sitei = __shfl_sync(FULL, site, i);
+            const int snewi = __shfl_sync(FULL, snew, i);
+            const uint32_t w2i = __shfl_sync(FULL, w2, i);
+            const int kp = k + dki;
+            bool acc = dki == 0;
+            if (!acc && kp >= lo && kp <= hi) {
+                acc = exact_decision(glng, gH, Hs, lo, k, kp, k0, 0, lnf, frozen, w2i);
+                if (scr < 0) ++nex;
+                else if ((int)acc != scr) ++nmis;
+            }
+            if (acc) {
+                sp[sitei] = (int8_t)snewi;
+                k = kp;
+                ++nacc;
+            }
+            if (!frozen && lane == 0) {
+                Hs[k - lo] += 1u;
+                V[k - lo] += lnfq;
+            }
+            if (REPLAY && lane == 0) {
+                c.acc_out[(size_t)slot * T + t] = acc ? 1 : 0;
+                c.dk_out[(size_t)slot * T + t] = dki;
+            }
+            t += 1;
+            __syncwarp();
+        }
     }
 
     // ---- write back lattice, float64 ln g (rebuilt exactly), H, counters
@@ -239,10 +359,11 @@ __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
         for (int i = lane; i < s.N; i += 32) gsp[i] = sp[i];
     }
     if (!frozen) {
+        double *gl = s.lng + (size_t)slot * s.W;
         for (int b = lane; b < nb; b += 32) {
             const uint32_t h1 = Hs[b], h0 = gH[b];
             if (h1 != h0) {
-                glng[b] = seqadd(glng[b], lnf, h1 - h0);
+                gl[b] = seqadd(gl[b], lnf, h1 - h0);
                 gH[b] = h1;
             }
         }
@@ -263,19 +384,21 @@ cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st)
     const dim3 grid((s.nw + G - 1) / G), block(32 * G);
     const bool ising = s.model == 0;
     cudaError_t e;
-#define REWL_LAUNCH_MOVE(I, R)                                                                   \
+#define REWL_LAUNCH_MOVE(I, R, C)                                                                \
     do {                                                                                         \
-        e = cudaFuncSetAttribute(k_move<I, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+        e = cudaFuncSetAttribute(k_move<I, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                  (int)smem);                                                     \
         if (e != cudaSuccess) return e;                                                          \
-        k_move<I, R><<<grid, block, smem, st>>>(s, c);                                           \
+        k_move<I, R, C><<<grid, block, smem, st>>>(s, c);                                        \
     } while (0)
     if (ising) {
-        if (c.words) REWL_LAUNCH_MOVE(true, true);
-        else REWL_LAUNCH_MOVE(true, false);
+        if (c.words) REWL_LAUNCH_MOVE(true, true, false);
+        else if (c.check_all) REWL_LAUNCH_MOVE(true, false, true);
+        else REWL_LAUNCH_MOVE(true, false, false);
     } else {
-        if (c.words) REWL_LAUNCH_MOVE(false, true);
-        else REWL_LAUNCH_MOVE(false, false);
+        if (c.words) REWL_LAUNCH_MOVE(false, true, false);
+        else if (c.check_all) REWL_LAUNCH_MOVE(false, false, true);
+        else REWL_LAUNCH_MOVE(false, false, false);
     }
 #undef REWL_LAUNCH_MOVE
     return cudaGetLastError();

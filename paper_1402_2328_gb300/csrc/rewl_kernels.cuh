@@ -53,10 +53,10 @@ struct MoveCfg {
 };
 
 // Shared memory of one walker in the move kernel: lattice (16-byte padded), int64 ln g
-// shadow and uint32 H over the window (padded to 4 bins).
+// shadow and uint32 H over the window (padded to 4 bins), uint32 claim stamps per site.
 __host__ __device__ inline size_t move_smem_per_walker(int N, int W)
 {
-    return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 12u;
+    return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 12u + (size_t)((N + 3) & ~3) * 4u;
 }
 cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st);
 cudaError_t launch_init_prep(const State &s, long long prep_budget, cudaStream_t st);

@@ -165,11 +165,12 @@ def test_replay_bit_exact(cuda_lib, model, L, n, T, W, scale):
 
 
 # ------------------------------------------------------------------ whole runs
+@pytest.mark.parametrize("check", [0, 1])
 @pytest.mark.parametrize("model,L,h,m,rounds,interval", [
     (0, 8, 4, 2, 60, 1000), (3, 6, 3, 3, 60, 700), (0, 16, 8, 4, 25, 2000),
     (10, 12, 8, 2, 25, 1500), (0, 5, 2, 3, 80, 333), (0, 8, 1, 1, 50, 1000)])
-def test_rounds_bit_exact(model, L, h, m, rounds, interval):
-    g, o = _pair(model, L, h, m, seed=11 + L, interval=interval, check_all=1)
+def test_rounds_bit_exact(model, L, h, m, rounds, interval, check):
+    g, o = _pair(model, L, h, m, seed=11 + L, interval=interval, check_all=check)
     g.init()
     assert o.init() == 0
     _same(g.state(), o.state())
