@@ -251,38 +251,57 @@ __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
         // a step that is too close to call in float32 or whose k' leaves the cache is only
         // flagged, and the batch is cut at the first flagged step afterwards (the steps after
         // it are discarded), so no bookkeeping sits on the dependency chain.
-        const float thrA = thr + M; // sure accept: thr + M < d
-        const float thrR = thr - M; // sure reject: thr - M > d
-        int kc = k;
+        // Steps are resolved in pairs (2p, 2p+1): the three cache lookups a pair can need
+        // (k' of the first step; k' of the second step after the first moved / stayed) are
+        // issued together, so one shuffle latency covers two moves.  Decision variable:
+        // e = ln g(k) - ln g(k') - thr; accept if e > M, reject if e < -M, else unsure.
+        int xk = 16; // cache offset of the current bin
         float Lk = 0.0f;
         unsigned accbits = 0u, badbits = 0u, saccbits = 0u, srejbits = 0u;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            if ((i & 7) == 0 && i > 0 && (badbits != 0u || i >= J)) break;
-            const int dki = __shfl_sync(FULL, dk, i);
-            const float tA = __shfl_sync(FULL, thrA, i);
-            const float tR = __shfl_sync(FULL, thrR, i);
-            const int kp = kc + dki;
-            const int xo = kp - base;
-            const float Lkp = __shfl_sync(FULL, Lw, xo & 31);
-            const float d = Lk - Lkp;
-            const bool dz = dki == 0;
-            const bool a0 = tA < d;
-            const bool act = dz || a0;
-            // CHECK: every in-window move is also decided by the float64 path, and the float32
-            // verdict is kept to count disagreements
-            const bool unsure = CHECK ? (Lkp < INFINITY) : !(tR > d);
-            const bool bad = (unsigned)xo >= 32u || (!dz && (CHECK ? unsure : (!a0 && unsure)));
-            badbits |= bad ? (1u << i) : 0u;
+        for (int p = 0; p < 16; ++p) {
+            const int i = 2 * p;
+            if ((p & 3) == 0 && p > 0 && (badbits != 0u || i >= J)) break;
+            const int dk0 = __shfl_sync(FULL, dk, i), dk1 = __shfl_sync(FULL, dk, i + 1);
+            const float th0 = __shfl_sync(FULL, thr, i), th1 = __shfl_sync(FULL, thr, i + 1);
+            const int x0 = xk + dk0;       // k' of step i
+            const int xA = x0 + dk1;       // k' of step i+1 if step i moved
+            const int xR = xk + dk1;       // k' of step i+1 if step i stayed
+            const float L0 = __shfl_sync(FULL, Lw, x0 & 31);
+            const float LA_ = __shfl_sync(FULL, Lw, xA & 31);
+            const float LR = __shfl_sync(FULL, Lw, xR & 31);
+            // step i
+            const bool dz0 = dk0 == 0;
+            const float e0 = (Lk - L0) - th0;
+            const bool a0 = dz0 || e0 > M;
+            const bool moved0 = a0 && !dz0;
+            const bool un0 = !dz0 && (CHECK ? (L0 < INFINITY) : !(fabsf(e0) > M));
+            const bool bad0 = (unsigned)x0 >= 32u || un0;
+            // step i+1 in the world the first step chose
+            const float LA = (dk1 == -dk0) ? Lk : LA_; // back to the bin just left
+            const float Lm = L0 + lnf_f;               // value after step i if moved
+            const float Ls = Lk + lnf_f;               // value after step i if stayed
+            const float Lc1 = moved0 ? Lm : Ls;
+            const float L1 = moved0 ? LA : LR;
+            const int x1 = moved0 ? xA : xR;
+            const int xc1 = moved0 ? x0 : xk;
+            const bool dz1 = dk1 == 0;
+            const float e1 = (Lc1 - L1) - th1;
+            const bool a1 = dz1 || e1 > M;
+            const bool moved1 = a1 && !dz1;
+            const bool un1 = !dz1 && (CHECK ? (L1 < INFINITY) : !(fabsf(e1) > M));
+            const bool bad1 = (unsigned)x1 >= 32u || un1;
+            // write back the running values of the bins left
+            if (moved0 && lane == xk) Lw = Lk;
+            if (moved1 && lane == xc1) Lw = Lc1;
+            xk = moved1 ? x1 : xc1;
+            Lk = (moved1 ? L1 : Lc1) + lnf_f;
+            accbits |= (a0 ? (1u << i) : 0u) | (a1 ? (2u << i) : 0u);
+            badbits |= (bad0 ? (1u << i) : 0u) | (bad1 ? (2u << i) : 0u);
             if (CHECK) {
-                saccbits |= a0 ? (1u << i) : 0u;
-                srejbits |= (tR > d) ? (1u << i) : 0u;
+                saccbits |= (e0 > M ? (1u << i) : 0u) | (e1 > M ? (2u << i) : 0u);
+                srejbits |= (e0 < -M ? (1u << i) : 0u) | (e1 < -M ? (2u << i) : 0u);
             }
-            const bool leave = act && !dz;
-            if (leave && lane == kc - base) Lw = Lk; // keep the running value of the bin left
-            kc = act ? kp : kc;
-            Lk = (leave ? Lkp : Lk) + lnf_f;
-            accbits |= act ? (1u << i) : 0u;
         }
         const unsigned stopbits = badbits | (J >= 32 ? 0u : (0xffffffffu << J));
         const int ndone = stopbits ? __ffs(stopbits) - 1 : 32;
@@ -296,7 +315,7 @@ __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
             if (lane >= o) pos += v;
         }
         const int mypos = k + pos;
-        kc = ndone > 0 ? k + __shfl_sync(FULL, pos, ndone - 1) : k;
+        const int kc = ndone > 0 ? k + __shfl_sync(FULL, pos, ndone - 1) : k;
         // float32 verdict at the cut (CHECK): 1 sure accept, 0 sure reject, -1 unsure
         const int scr = !CHECK || ndone >= 32 ? -1
                         : (((saccbits >> ndone) & 1u) ? 1 : (((srejbits >> ndone) & 1u) ? 0 : -1));
