@@ -223,6 +223,27 @@ int rewl_replay(int model, int L, int n, int W, int T, void *spins, void *k, con
                 const void *words, void *acc, void *dk, void *stream);
 
 /*
+ * rewl_replay_static -- rewl_replay that allocates nothing.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc, e.g. code that draws all device
+ * memory from its own pool (a framework's caching allocator holding most of the GPU), or
+ * code that must not stall the device (rewl_replay's cudaFree of its per-call scratch waits
+ * for the GPU).  Same arguments, results and errors as rewl_replay; the caller still owns
+ * and passes every input and output.  The per-case scratch of the move kernel (step and
+ * acceptance counters and the run status) lives instead in one fixed device array of the
+ * library, sized for REWL_REPLAY_STATIC_MAX_N cases (about 256 KB, held on every GPU that
+ * loads the library until the process exits); n > REWL_REPLAY_STATIC_MAX_N fails with
+ * INVALID_ARG.  The first call on a device looks the array's device address up on that
+ * device (cudaGetSymbolAddress); make that first call before any stream capture.  Every call
+ * zeroes the part of the array it uses and then overwrites it, so the array keeps the last
+ * call's contents, and calls whose work overlaps on the GPU (other streams, other threads)
+ * race on it: serialise them.
+ */
+#define REWL_REPLAY_STATIC_MAX_N 16384
+int rewl_replay_static(int model, int L, int n, int W, int T, void *spins, void *k,
+                       const void *lo, const void *hi, void *lng, void *H, const void *lnf,
+                       const void *frozen, const void *words, void *acc, void *dk, void *stream);
+
+/*
  * Diagnostics of the arithmetic the moves depend on (device pointers, stream or NULL):
  *   rewl_philox: out[i][0..3] = Philox4x32-10(ctr[i][0..3], key[i][0..1]) for i < n
  *     (Salmon et al., SC'11).

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -927,6 +928,135 @@ int rewl_replay(int model, int L, int n, int W, int T, void *spins, void *k, con
     if (hs.err) {
         g_err = (hs.err & ERR_INPUT) ? "rewl_replay: k outside [lo, hi] or window wider than W"
                                      : "rewl_replay: ln g or ln f out of the supported range";
+        return REWL_ERR_INVALID_ARG;
+    }
+    return REWL_OK;
+}
+
+} // extern "C"
+
+// ---- replay without allocation: the per-case scratch of the move kernel (step and
+// acceptance counters, run status) lives in one fixed device array instead of cudaMalloc.
+namespace {
+struct ReplayScratch {
+    unsigned long long step[REWL_REPLAY_STATIC_MAX_N];
+    unsigned long long acc[REWL_REPLAY_STATIC_MAX_N];
+    DevStatus status;
+};
+constexpr int SCRATCH_MAX_DEVICES = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[SCRATCH_MAX_DEVICES] = {};
+} // namespace
+
+// Every GPU that loads the library holds this array (about 256 KB) until the process exits.
+static __device__ __align__(256) unsigned char g_replay_scratch[sizeof(ReplayScratch)];
+
+// Device address of g_replay_scratch on the current device.  The first call on a device looks
+// it up (cudaGetSymbolAddress, with that device current); later calls reuse the address.
+static int replay_scratch(ReplayScratch **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        g_err = std::string("rewl_replay_static: cudaGetDevice: ") + cudaGetErrorString(e);
+        return REWL_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= SCRATCH_MAX_DEVICES) {
+        g_err = "rewl_replay_static: device index out of range";
+        return REWL_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_replay_scratch);
+        if (e != cudaSuccess || !p) {
+            g_err = std::string("rewl_replay_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return REWL_ERR_CUDA;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<ReplayScratch *>(g_scratch_addr[dev]);
+    return REWL_OK;
+}
+
+extern "C" {
+
+int rewl_replay_static(int model, int L, int n, int W, int T, void *spins, void *k, const void *lo,
+                       const void *hi, void *lng, void *H, const void *lnf, const void *frozen,
+                       const void *words, void *acc, void *dk, void *stream)
+{
+    if (n < 0 || L < 2 || L > 255 || W < 1 || T < 1 || T > 100000000 || (model != 0 && (model < 2 || model > 127)) ||
+        !spins || !k || !lo || !hi || !lng || !H || !lnf || !frozen || !words || !acc || !dk) {
+        g_err = "rewl_replay_static: invalid argument";
+        return REWL_ERR_INVALID_ARG;
+    }
+    if (n > REWL_REPLAY_STATIC_MAX_N) {
+        g_err = "rewl_replay_static: n exceeds REWL_REPLAY_STATIC_MAX_N (" +
+                std::to_string(REWL_REPLAY_STATIC_MAX_N) + ") cases";
+        return REWL_ERR_INVALID_ARG;
+    }
+    if (n == 0) return REWL_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    State s{};
+    s.model = model;
+    s.q = model == 0 ? 2 : model;
+    s.L = L;
+    s.N = L * L;
+    s.nw = n;
+    s.m = 1;
+    s.h = n;
+    s.W = W;
+    s.spin_stride = s.N;
+    s.vec_spins = (s.N & 15) == 0 && ((uintptr_t)spins & 15) == 0;
+    s.magic = (uint32_t)((0x100000000ULL + (uint64_t)L - 1) / (uint64_t)L);
+    for (uint32_t site = 0; site < (uint32_t)s.N; ++site)
+        if ((uint32_t)(((uint64_t)site * s.magic) >> 32) != site / (uint32_t)L) {
+            g_err = "rewl_replay_static: lattice too large";
+            return REWL_ERR_INVALID_ARG;
+        }
+    if (move_smem_per_walker(s.N, W) > MAX_SMEM_PER_CTA) {
+        g_err = "rewl_replay_static: lattice and window do not fit in shared memory";
+        return REWL_ERR_INVALID_ARG;
+    }
+    ReplayScratch *sc = nullptr;
+    int rc = replay_scratch(&sc);
+    if (rc != REWL_OK) return rc;
+    s.spins = (int8_t *)spins;
+    s.cfg = nullptr;
+    s.k = (int *)k;
+    s.lng = (double *)lng;
+    s.H = (uint32_t *)H;
+    s.lo = (const int *)lo;
+    s.hi = (const int *)hi;
+    s.lnf = (double *)lnf;
+    s.finished = (uint8_t *)frozen;
+    s.step = sc->step;
+    s.acc = sc->acc;
+    s.status = &sc->status;
+    // the array keeps the previous call's contents: the counters and the status start at zero
+    cudaError_t e = cudaMemsetAsync(sc->step, 0, (size_t)n * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->acc, 0, (size_t)n * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&sc->status, 0, sizeof(DevStatus), st);
+    MoveCfg c{};
+    c.T = T;
+    c.walkers_per_block = 4;
+    while (c.walkers_per_block > 1 && (size_t)c.walkers_per_block * move_smem_per_walker(s.N, W) > MAX_SMEM_PER_CTA)
+        c.walkers_per_block >>= 1;
+    c.eps_l = LNU32_EPS;
+    c.words = (const uint32_t *)words;
+    c.acc_out = (int *)acc;
+    c.dk_out = (int *)dk;
+    if (e == cudaSuccess) e = launch_move(s, c, st);
+    DevStatus hs{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, &sc->status, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        g_err = std::string("rewl_replay_static: ") + cudaGetErrorString(e);
+        return REWL_ERR_CUDA;
+    }
+    if (hs.err) {
+        g_err = (hs.err & ERR_INPUT) ? "rewl_replay_static: k outside [lo, hi] or window wider than W"
+                                     : "rewl_replay_static: ln g or ln f out of the supported range";
         return REWL_ERR_INVALID_ARG;
     }
     return REWL_OK;

@@ -62,6 +62,7 @@ def lib():
             "rewl_destroy": ([P], None),
             "rewl_last_error": ([P], C.c_char_p),
             "rewl_replay": ([I, I, I, I, I] + [P] * 12, I),
+            "rewl_replay_static": ([I, I, I, I, I] + [P] * 12, I),
             "rewl_philox": ([P, P, P, I, P], I),
             "rewl_lnu": ([P, P, I, P], I),
             "rewl_lnu_bound": ([C.c_uint64, C.c_uint64, P, P, P], I),
@@ -251,6 +252,19 @@ def replay(model, L, spins, k, lo, hi, lng, H, lnf, frozen, words, acc, dk, stre
     _check(lib().rewl_replay(model, L, n, W, T, _ptr(spins), _ptr(k), _ptr(lo), _ptr(hi),
                              _ptr(lng), _ptr(H), _ptr(lnf), _ptr(frozen), _ptr(words), _ptr(acc),
                              _ptr(dk), _stream_ptr(stream)))
+
+
+REPLAY_STATIC_MAX_N = 16384
+
+
+def replay_static(model, L, spins, k, lo, hi, lng, H, lnf, frozen, words, acc, dk, stream=None):
+    """replay() without any device allocation (scratch in a fixed library array, at most
+    REPLAY_STATIC_MAX_N cases per call; calls overlapping on the GPU race on it)."""
+    n, T = words.shape[0], words.shape[1]
+    W = lng.shape[1]
+    _check(lib().rewl_replay_static(model, L, n, W, T, _ptr(spins), _ptr(k), _ptr(lo), _ptr(hi),
+                                    _ptr(lng), _ptr(H), _ptr(lnf), _ptr(frozen), _ptr(words),
+                                    _ptr(acc), _ptr(dk), _stream_ptr(stream)))
 
 
 def philox(ctr, key, out, stream=None):
