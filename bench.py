@@ -39,7 +39,22 @@ WORKLOADS = {
                                 lnf_final=1e-8, flatness=0.8, interval=10_000, config_id=3),
     "ising_L8_h4_m1": dict(model=0, L=8, windows=4, walkers=1, overlap=0.75,
                            lnf_final=1e-6, flatness=0.8, interval=10_000, config_id=1),
+    # 24 uneven instances in one launch per round: (model, L) cycles Ising 16/32/64 and
+    # q=10 Potts 20/40; windows [8,16,32,64][i%4]; walkers [4,8,16][(i//4)%3]; 6720 walkers
+    "batch24_uneven": dict(batch=True, interval=10_000, config_id=4, lnf_final=1e-8,
+                           flatness=0.8, overlap=0.75),
 }
+
+
+def batch24_descs(wl, rank=0):
+    out = []
+    for i in range(24):
+        model, L = [(0, 16), (0, 32), (0, 64), (10, 20), (10, 40)][i % 5]
+        out.append(dict(model=model, L=L, windows=[8, 16, 32, 64][i % 4],
+                        walkers=[4, 8, 16][(i // 4) % 3], lnf_final=wl["lnf_final"],
+                        flatness=wl["flatness"], overlap=wl["overlap"],
+                        seed=seed_for(wl["config_id"], 100 * rank + i), instance=i))
+    return out
 METRIC = "WL flip attempts/s"
 UNIT = "attempts/s"
 # Algorithmic integer work of one WL attempt (Philox4x32-10 call, site and neighbour index
@@ -133,6 +148,108 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- main arms
+def _roofline(per_launch_attempts, move_ms, move_launches, sms, step_ms):
+    peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tinst = sms * 128 * sm_max_mhz * 1e6 / 1e12
+    move_avg_s = (move_ms / max(move_launches, 1)) / 1e3
+    achieved = ALG_INSTR_PER_ATTEMPT * per_launch_attempts / move_avg_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
+            "frac": achieved / peak_tinst, "traffic": None, "kernel": "k_move",
+            "kernel_ms_avg": move_avg_s * 1e3,
+            "kernel_share_of_step": move_ms / step_ms if step_ms else None,
+            "alg_inst_per_attempt": ALG_INSTR_PER_ATTEMPT,
+            "peak_basis": f"{sms} SMs x 128 lanes x {sm_max_mhz:.0f} MHz (max SM clock), of measured"}
+
+
+def run_gpu_batch(args, wl, rank, world):
+    """Config-4 batch: aggregate attempts/s of 24 uneven instances advanced by one move launch
+    per round (autotuned walkers per CTA), against the same instances run one at a time."""
+    import torch
+    import paper_1402_2328_gb300.rewl as R
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    descs = batch24_descs(wl, rank)
+    b = R.REWLBatch(descs, interval=wl["interval"], stream=stream)
+    b.init()
+    best, trial = b.autotune(rounds=1)  # 4 rounds of the simulation itself, untimed
+    info = b.info()
+    per_round = info["walkers"] * wl["interval"]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    b.set_param("profile", 1)
+    b.kernel_time(reset=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(dev) as clk:
+        for a, z in evs:
+            flush.zero_()
+            a.record(stream)
+            b.step(1)
+            z.record(stream)
+        torch.cuda.synchronize()
+    step_ms = sum(a.elapsed_time(z) for a, z in evs)
+    move_ms, move_launches = b.kernel_time(reset=True)
+    b.set_param("profile", 0)
+    # e2e: the blocking public call per round + window ln g of every instance back to host
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.run(max_rounds=1)
+        for i in range(len(descs)):
+            x = b.instance(i).get_state("lng_mean")
+            d2h += x.nbytes
+    e2e_s = time.perf_counter() - t0
+    b.close()
+    # the same instances one at a time (each with its own launches), same number of rounds
+    solo_ms = 0.0
+    for d in descs:
+        g = R.REWL(d["model"], d["L"], d["windows"], d["overlap"], d["walkers"], d["lnf_final"],
+                   d["flatness"], seed=d["seed"], instance=d["instance"],
+                   interval=wl["interval"], stream=stream)
+        g.init()
+        g.step(args.warmup)
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        g.step(args.steps)
+        z.record(stream)
+        torch.cuda.synchronize()
+        solo_ms += a.elapsed_time(z)
+        g.close()
+    t_max = step_ms
+    if world > 1:
+        t = torch.tensor([step_ms, e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max, e2e_s = float(t[0]), float(t[1])
+    attempts = per_round * args.steps * world
+    return {
+        "metric": METRIC, "value": attempts / (t_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "instances": len(descs), "walkers": info["walkers"],
+                   "interval": wl["interval"], "attempts_per_step": per_round * world,
+                   "ctas_per_launch": info["ctas"], "autotuned_walkers_per_cta": best,
+                   "autotune_ms_per_round": trial,
+                   "parallelism": f"replicas{world}" if world > 1 else "1gpu",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "roofline": _roofline(per_round, move_ms, move_launches, sms, step_ms),
+        "one_at_a_time": {"value": per_round * args.steps / (solo_ms / 1e3), "unit": UNIT,
+                          "ms_per_step": solo_ms / args.steps},
+        "e2e": {"value": attempts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": d2h // max(args.steps, 1),
+                "call": "rewl_batch_run(1 round) + rewl_get_state(lng_mean) of each instance"},
+        "gpu_launches": 4 * args.steps, "clocks": clk.summary(),
+    }
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     import paper_1402_2328_gb300.rewl as R
@@ -264,7 +381,7 @@ def main():
         return
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not wl.get("batch"):
         # spawn the oracle pool before the first CUDA call
         val, tmax, attempts = oracle_throughput(wl, procs, args.cpu_rounds)
         cpu = {"value": val, "unit": UNIT, "cores": procs, "kind": "oracle",
@@ -273,7 +390,7 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    out = run_gpu(args, wl, rank, world)
+    out = run_gpu_batch(args, wl, rank, world) if wl.get("batch") else run_gpu(args, wl, rank, world)
     if rank == 0:
         if cpu is not None:
             out["cpu_baseline"] = cpu

@@ -207,6 +207,53 @@ void rewl_destroy(rewl_t r);
 const char *rewl_last_error(rewl_t r);
 
 /*
+ * Batched instances.  Many independent REWL simulations (any mix of models, L, window
+ * counts, walkers per window; each with its own seed and instance id) advanced together,
+ * round by round: one move-kernel launch whose CTAs each serve up to `walkers_per_block`
+ * walkers of one instance, then batched flatness/advance, exchange and round-end kernels,
+ * rounds captured in CUDA graphs.  Every instance evolves bit for bit as it would alone with
+ * rewl_create/rewl_run (same parameters, seed, instance id and interval).
+ */
+typedef struct rewl_batch_s *rewl_batch_t;
+typedef struct {
+    int model;              /* 0 = Ising, q >= 2 = q-state Potts */
+    int L, windows, walkers_per_window;
+    double overlap, lnf_final, flatness;
+    double lnf_init;        /* <= 0: default 1 */
+    uint64_t seed;
+    int instance;           /* enters the random stream (0..2^24-1) */
+} rewl_desc_t;
+
+/* n instances (host array of descriptors), all with the same moves-per-round `interval`. */
+int rewl_batch_create(rewl_batch_t *out, const rewl_desc_t *descs, int n, long long interval);
+/* Keys: "walkers_per_block" (upper bound of walkers per CTA, 0 = automatic), "graph_rounds",
+ * "profile" (time the move kernel with events, rewl_batch_kernel_time), "check_all",
+ * "prep_budget" (before init). */
+int rewl_batch_set_param(rewl_batch_t b, const char *key, double value);
+int rewl_batch_set_stream(rewl_batch_t b, void *stream);
+/* Seeds and preps every instance (rewl_init) and builds the device tables. */
+int rewl_batch_init(rewl_batch_t b);
+/* Enqueue `rounds` rounds without waiting (rounds of finished instances do nothing). */
+int rewl_batch_step(rewl_batch_t b, int rounds);
+/* Run until every instance is done, max_rounds (< 0: no limit) or max_seconds (<= 0: none). */
+int rewl_batch_run(rewl_batch_t b, double max_seconds, long long max_rounds, int *status);
+/*
+ * Autotuner: times `rounds` rounds with each walkers-per-CTA bound in {2, 4, 8, 16} and keeps
+ * the fastest.  The trial rounds are ordinary rounds of the simulation (results do not depend
+ * on the launch configuration).  best (may be NULL) gets the choice, ms (may be NULL, 4
+ * doubles) the measured milliseconds per round of each candidate.
+ */
+int rewl_batch_autotune(rewl_batch_t b, int rounds, int *best, double *ms);
+/* Instance i as a handle for the query calls (get_state, get_lng, stitch, stats,
+ * checkpoint); owned by the batch: do not destroy it or run it on its own. */
+int rewl_batch_instance(rewl_batch_t b, int i, rewl_t *out);
+/* out (4 ints): instances, total walkers, CTAs of the move launch, warps per CTA. */
+int rewl_batch_info(rewl_batch_t b, int *out);
+int rewl_batch_kernel_time(rewl_batch_t b, double *move_ms, long long *launches, int reset);
+void rewl_batch_destroy(rewl_batch_t b);
+const char *rewl_batch_last_error(rewl_batch_t b);
+
+/*
  * rewl_replay -- n independent WL attempt sequences of T steps each, on caller state, with
  * caller-given random words instead of Philox (the move of Sec. 2 exactly as rewl_run
  * performs it, same kernel).  All pointers are device pointers:

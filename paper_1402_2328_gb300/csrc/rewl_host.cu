@@ -17,12 +17,13 @@
 #include "rewl.h"
 #include "rewl_device.cuh"
 #include "rewl_kernels.cuh"
+#include "rewl_handle.h"
 
 using namespace rewl;
 
-namespace {
+thread_local std::string g_err; // message of the last failed call without a handle
 
-thread_local std::string g_err;
+namespace {
 
 template <typename T> T *dmalloc(size_t n, cudaError_t &e)
 {
@@ -72,46 +73,6 @@ int check_windows(int B, const std::vector<int> &lo, const std::vector<int> &hi)
 }
 
 } // namespace
-
-struct rewl_s {
-    // parameters
-    int model = 0, q = 2, L = 0, N = 0, B = 0, h = 0, m = 0, nw = 0, W = 0;
-    double overlap = 0.75, lnf_final = 1e-8, flatness = 0.8, lnf_init = 1.0;
-    uint64_t seed = 0;
-    uint32_t inst = 0;
-    long long interval = 10000, prep_budget = 100;
-    int graph_rounds = 32, wpb = 0, check_all = 0, profile = 0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free; // move-kernel timing
-    std::vector<int> lo, hi;
-    std::vector<double> lng_init;
-    bool inited = false, allocated = false;
-    cudaStream_t stream = nullptr;
-    // device state
-    State st{};
-    int *d_lohi = nullptr;
-    double *d_mean = nullptr, *d_out = nullptr;
-    int *d_joins = nullptr, *d_ok = nullptr;
-    DevStatus *h_status = nullptr; // pinned
-    // graphs
-    cudaGraphExec_t graph = nullptr;
-    int graph_len = 0;
-    // bookkeeping
-    std::string err;
-    double seconds = 0.0;
-    std::atomic<int> abort_flag{0};
-    int sms = 148;
-
-    int fail(int code, const std::string &msg)
-    {
-        err = msg;
-        g_err = msg;
-        return code;
-    }
-    int cuda_fail(cudaError_t e, const char *where)
-    {
-        return fail(REWL_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
-    }
-};
 
 static int walkers_per_block(const rewl_t r)
 {
@@ -374,7 +335,7 @@ int rewl_init(rewl_t r)
     return REWL_OK;
 }
 
-static cudaError_t enqueue_round(rewl_t r)
+cudaError_t rewl_enqueue_round(rewl_t r)
 {
     MoveCfg c{};
     c.T = (int)r->interval;
@@ -417,7 +378,7 @@ static int build_graph(rewl_t r, int len)
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     const int prof = r->profile;
     r->profile = 0;
-    for (int i = 0; i < len && e == cudaSuccess; ++i) e = enqueue_round(r);
+    for (int i = 0; i < len && e == cudaSuccess; ++i) e = rewl_enqueue_round(r);
     r->profile = prof;
     cudaError_t e2 = cudaStreamEndCapture(cap, &g);
     r->stream = saved;
@@ -484,7 +445,7 @@ int rewl_run(rewl_t r, double max_seconds, long long max_rounds, int *status)
             n = gl;
             e = cudaGraphLaunch(r->graph, r->stream);
         } else {
-            for (long long i = 0; i < n && e == cudaSuccess; ++i) e = enqueue_round(r);
+            for (long long i = 0; i < n && e == cudaSuccess; ++i) e = rewl_enqueue_round(r);
         }
         if (e != cudaSuccess) {
             rc = r->cuda_fail(e, "rewl_run launch");
@@ -508,7 +469,7 @@ int rewl_step(rewl_t r, int rounds)
     if (!r || rounds < 0) return REWL_ERR_INVALID_ARG;
     if (!r->inited) return r->fail(REWL_ERR_STATE, "rewl_step before rewl_init");
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < rounds && e == cudaSuccess; ++i) e = enqueue_round(r);
+    for (int i = 0; i < rounds && e == cudaSuccess; ++i) e = rewl_enqueue_round(r);
     if (e != cudaSuccess) return r->cuda_fail(e, "rewl_step");
     return REWL_OK;
 }

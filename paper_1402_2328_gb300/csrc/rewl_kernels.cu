@@ -118,17 +118,12 @@ __device__ __noinline__ bool exact_decision(const double *glng, const uint32_t *
     return (d >= 0.0) || (lnu64(w2) < d);
 }
 
+// One walker's `c.T` moves; `base` is the walker's shared-memory block, the whole warp calls.
 template <bool ISING, bool REPLAY, bool CHECK>
-__global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
+__device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, const int slot,
+                                            unsigned char *base, const int lane)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int slot = blockIdx.x * c.walkers_per_block + wib;
-    if (slot >= s.nw) return;
     if (s.status != nullptr && s.status->done) return;
-
-    const size_t per = move_smem_per_walker(s.N, s.W);
-    unsigned char *base = smem + (size_t)wib * per;
     int8_t *sp = reinterpret_cast<int8_t *>(base);
     long long *V = reinterpret_cast<long long *>(base + pad16(s.N));
     uint32_t *Hs = reinterpret_cast<uint32_t *>(V + padw(s.W));
@@ -396,6 +391,50 @@ __global__ void __launch_bounds__(512) k_move(State s, MoveCfg c)
     }
 }
 
+template <bool ISING, bool REPLAY, bool CHECK>
+__global__ void __launch_bounds__(512, 1) k_move(State s, MoveCfg c)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int slot = blockIdx.x * c.walkers_per_block + wib;
+    if (slot >= s.nw) return;
+    move_walker<ISING, REPLAY, CHECK>(s, c, slot, smem + (size_t)wib * move_smem_per_walker(s.N, s.W),
+                                      lane);
+}
+
+// Batched instances in one launch: CTA b serves walkers jobs[b].y .. jobs[b].y + jobs[b].z - 1 of
+// instance jobs[b].x; the model is chosen per CTA.
+template <bool CHECK>
+__global__ void __launch_bounds__(512, 1) k_move_batch(const State *__restrict__ states,
+                                                    const int4 *__restrict__ jobs, MoveCfg c)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int4 job = jobs[blockIdx.x];
+    if (wib >= job.z) return;
+    const State s = states[job.x];
+    unsigned char *base = smem + (size_t)wib * move_smem_per_walker(s.N, s.W);
+    if (s.model == 0) move_walker<true, false, CHECK>(s, c, job.y + wib, base, lane);
+    else move_walker<false, false, CHECK>(s, c, job.y + wib, base, lane);
+}
+
+cudaError_t launch_move_batch(const State *states, const int4 *jobs, int njobs, int walkers_per_block,
+                              size_t smem, const MoveCfg &c, cudaStream_t st)
+{
+    if (njobs <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (c.check_all) {
+        e = cudaFuncSetAttribute(k_move_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_move_batch<true><<<njobs, 32 * walkers_per_block, smem, st>>>(states, jobs, c);
+    } else {
+        e = cudaFuncSetAttribute(k_move_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_move_batch<false><<<njobs, 32 * walkers_per_block, smem, st>>>(states, jobs, c);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st)
 {
     const int G = c.walkers_per_block;
@@ -502,9 +541,9 @@ cudaError_t launch_init_prep(const State &s, long long prep_budget, cudaStream_t
 // ---------------------------------------------------------------------------------------
 // Flatness + window advance (Sec. 2).  One CTA per window.
 // ---------------------------------------------------------------------------------------
-__global__ void k_check(State s, double flatness, double lnf_final)
+__device__ __forceinline__ void check_window(const State &s, const int w, const double flatness,
+                                             const double lnf_final)
 {
-    const int w = blockIdx.x;
     if (s.status->done || s.finished[w]) return;
     const int m = s.m, W = s.W, nb = s.hi[w] - s.lo[w] + 1;
     uint8_t *mask = s.mask + (size_t)w * W;
@@ -567,6 +606,29 @@ __global__ void k_check(State s, double flatness, double lnf_final)
     }
 }
 
+__global__ void k_check(State s, double flatness, double lnf_final)
+{
+    check_window(s, blockIdx.x, flatness, lnf_final);
+}
+
+// tab[b] = (instance, window); prm[instance] = (flatness, ln f_final)
+__global__ void k_check_batch(const State *__restrict__ states, const int2 *__restrict__ tab,
+                              const double2 *__restrict__ prm)
+{
+    const int2 t = tab[blockIdx.x];
+    const State s = states[t.x];
+    const double2 p = prm[t.x];
+    check_window(s, t.y, p.x, p.y);
+}
+
+cudaError_t launch_check_batch(const State *states, const int2 *tab, int n, const double2 *prm,
+                               cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_check_batch<<<n, 256, 0, st>>>(states, tab, prm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check(const State &s, double flatness, double lnf_final, cudaStream_t st)
 {
     k_check<<<s.h, 256, 0, st>>>(s, flatness, lnf_final);
@@ -578,11 +640,11 @@ cudaError_t launch_check(const State &s, double flatness, double lnf_final, cuda
 // lane 0 draws the partner permutation and the decisions (m is small), the swap itself
 // exchanges configuration indices and bins.
 // ---------------------------------------------------------------------------------------
-__global__ void k_swap(State s)
+__device__ __forceinline__ void swap_pair(const State &s, const int pair)
 {
     if (s.status->done) return;
     const long long rd = s.status->round;
-    const int w = 2 * blockIdx.x + (int)(rd & 1);
+    const int w = 2 * pair + (int)(rd & 1);
     if (w + 1 >= s.h || threadIdx.x != 0) return;
     const int m = s.m, W = s.W;
     __shared__ int perm[MAX_M];
@@ -624,6 +686,23 @@ __global__ void k_swap(State s)
     s.swap_acc[w] += acc;
 }
 
+__global__ void k_swap(State s) { swap_pair(s, blockIdx.x); }
+
+// tab[b] = (instance, pair index)
+__global__ void k_swap_batch(const State *__restrict__ states, const int2 *__restrict__ tab)
+{
+    const int2 t = tab[blockIdx.x];
+    const State s = states[t.x];
+    swap_pair(s, t.y);
+}
+
+cudaError_t launch_swap_batch(const State *states, const int2 *tab, int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_swap_batch<<<n, 32, 0, st>>>(states, tab);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_swap(const State &s, cudaStream_t st)
 {
     if (s.h < 2) return cudaSuccess;
@@ -631,13 +710,28 @@ cudaError_t launch_swap(const State &s, cudaStream_t st)
     return cudaGetLastError();
 }
 
-__global__ void k_round_end(State s)
+__device__ __forceinline__ void round_end(const State &s)
 {
     if (s.status->done) return;
     s.status->round += 1;
     int all = 1;
     for (int w = 0; w < s.h; ++w) all &= s.finished[w];
     if (all) s.status->done = 1;
+}
+
+__global__ void k_round_end(State s) { round_end(s); }
+
+__global__ void k_round_end_batch(const State *__restrict__ states, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) round_end(states[i]);
+}
+
+cudaError_t launch_round_end_batch(const State *states, int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_round_end_batch<<<(n + 63) / 64, 64, 0, st>>>(states, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_round_end(const State &s, cudaStream_t st)

@@ -59,6 +59,13 @@ __host__ __device__ inline size_t move_smem_per_walker(int N, int W)
     return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 12u + (size_t)((N + 3) & ~3) * 4u;
 }
 cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st);
+// Batched instances: states/jobs/tables are device arrays (see the kernels).
+cudaError_t launch_move_batch(const State *states, const int4 *jobs, int njobs, int walkers_per_block,
+                              size_t smem, const MoveCfg &c, cudaStream_t st);
+cudaError_t launch_check_batch(const State *states, const int2 *tab, int n, const double2 *prm,
+                               cudaStream_t st);
+cudaError_t launch_swap_batch(const State *states, const int2 *tab, int n, cudaStream_t st);
+cudaError_t launch_round_end_batch(const State *states, int n, cudaStream_t st);
 cudaError_t launch_init_prep(const State &s, long long prep_budget, cudaStream_t st);
 cudaError_t launch_check(const State &s, double flatness, double lnf_final, cudaStream_t st);
 cudaError_t launch_swap(const State &s, cudaStream_t st);

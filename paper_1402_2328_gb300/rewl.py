@@ -68,6 +68,18 @@ def lib():
             "rewl_lnu_bound": ([C.c_uint64, C.c_uint64, P, P, P], I),
             "rewl_lnu_eps": ([], D),
             "rewl_seqadd": ([P, P, P, P, I, P], I),
+            "rewl_batch_create": ([P, P, I, C.c_longlong], I),
+            "rewl_batch_set_param": ([P, C.c_char_p, D], I),
+            "rewl_batch_set_stream": ([P, P], I),
+            "rewl_batch_init": ([P], I),
+            "rewl_batch_step": ([P, I], I),
+            "rewl_batch_run": ([P, D, C.c_longlong, P], I),
+            "rewl_batch_autotune": ([P, I, P, P], I),
+            "rewl_batch_instance": ([P, I, P], I),
+            "rewl_batch_info": ([P, P], I),
+            "rewl_batch_kernel_time": ([P, P, P, I], I),
+            "rewl_batch_destroy": ([P], None),
+            "rewl_batch_last_error": ([P], C.c_char_p),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -121,6 +133,13 @@ _FIELDS = {
 }
 
 
+class _Desc(C.Structure):
+    _fields_ = [("model", C.c_int), ("L", C.c_int), ("windows", C.c_int),
+                ("walkers_per_window", C.c_int), ("overlap", C.c_double),
+                ("lnf_final", C.c_double), ("flatness", C.c_double), ("lnf_init", C.c_double),
+                ("seed", C.c_uint64), ("instance", C.c_int)]
+
+
 class REWL:
     """One REWL simulation on the current CUDA device (see include/rewl.h)."""
 
@@ -137,6 +156,16 @@ class REWL:
             self.set_param(key, v)
         self.set_stream(stream)
 
+    @classmethod
+    def _view(cls, handle):
+        """Non-owning view of a handle owned by a batch."""
+        obj = cls.__new__(cls)
+        obj._lib = lib()
+        obj._h = handle
+        obj._owned = False
+        obj._update_dims()
+        return obj
+
     def _update_dims(self):
         d = np.zeros(8, np.int32)
         _check(self._lib.rewl_dims(self._h, _ptr(d)), self._h)
@@ -144,9 +173,9 @@ class REWL:
         self.nw = self.h * self.m
 
     def close(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and getattr(self, "_owned", True):
             self._lib.rewl_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         self.close()
@@ -242,6 +271,78 @@ class REWL:
 
     def restore(self, path: str):
         _check(self._lib.rewl_restore(self._h, os.fsencode(path)), self._h)
+
+
+class REWLBatch:
+    """Many independent REWL instances advanced together (include/rewl.h, batched)."""
+
+    def __init__(self, descs, interval: int = 10_000, stream=None, **params):
+        self._lib = lib()
+        arr = (_Desc * len(descs))()
+        for a, d in zip(arr, descs):
+            a.model, a.L, a.windows = d["model"], d["L"], d["windows"]
+            a.walkers_per_window = d["walkers"]
+            a.overlap, a.lnf_final = d.get("overlap", 0.75), d["lnf_final"]
+            a.flatness, a.lnf_init = d.get("flatness", 0.8), d.get("lnf_init", 0.0)
+            a.seed, a.instance = int(d["seed"]) & (2 ** 64 - 1), d.get("instance", 0)
+        h = C.c_void_p()
+        rc = self._lib.rewl_batch_create(C.byref(h), arr, len(descs), int(interval))
+        if rc != 0:
+            raise REWLError(f"rewl error {rc}: {self._lib.rewl_batch_last_error(None).decode()}")
+        self._h = h
+        self.n = len(descs)
+        for k, v in params.items():
+            self.set_param(k, v)
+        self._check(self._lib.rewl_batch_set_stream(self._h, _stream_ptr(stream)))
+
+    def _check(self, rc):
+        if rc != 0:
+            raise REWLError(f"rewl error {rc}: {self._lib.rewl_batch_last_error(self._h).decode()}")
+
+    def set_param(self, key, value):
+        self._check(self._lib.rewl_batch_set_param(self._h, key.encode(), float(value)))
+
+    def init(self):
+        self._check(self._lib.rewl_batch_init(self._h))
+
+    def step(self, rounds: int = 1):
+        self._check(self._lib.rewl_batch_step(self._h, int(rounds)))
+
+    def run(self, max_seconds: float = 0.0, max_rounds: int = -1) -> str:
+        st = C.c_int(0)
+        self._check(self._lib.rewl_batch_run(self._h, float(max_seconds), int(max_rounds),
+                                             C.byref(st)))
+        return STATUS[st.value]
+
+    def autotune(self, rounds: int = 2):
+        best = C.c_int(0)
+        ms = (C.c_double * 4)()
+        self._check(self._lib.rewl_batch_autotune(self._h, int(rounds), C.byref(best), ms))
+        return best.value, dict(zip((2, 4, 8, 16), list(ms)))
+
+    def instance(self, i: int) -> REWL:
+        h = C.c_void_p()
+        self._check(self._lib.rewl_batch_instance(self._h, int(i), C.byref(h)))
+        return REWL._view(h)
+
+    def info(self):
+        out = np.zeros(4, np.int32)
+        self._check(self._lib.rewl_batch_info(self._h, _ptr(out)))
+        return dict(instances=int(out[0]), walkers=int(out[1]), ctas=int(out[2]),
+                    warps_per_cta=int(out[3]))
+
+    def kernel_time(self, reset: bool = True):
+        ms, n = C.c_double(), C.c_longlong()
+        self._check(self._lib.rewl_batch_kernel_time(self._h, C.byref(ms), C.byref(n), int(reset)))
+        return ms.value, n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rewl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 # ---- free functions (device tensors in, device tensors out)
