@@ -250,6 +250,65 @@ def run_gpu_batch(args, wl, rank, world):
     }
 
 
+def exact_lng_golden(model, L):
+    """Exact ln g from the committed golden files (Ising only), or None."""
+    if model != 0:
+        return None
+    g = os.path.join(ROOT, "tests", "golden")
+    for name in (f"ising_L{L}_lng.txt", f"ising_L{L}_counts.txt"):
+        path = os.path.join(g, name)
+        if os.path.exists(path):
+            vals = []
+            for line in open(path):
+                if line.startswith("#"):
+                    continue
+                v = line.split()[1]
+                if name.endswith("counts.txt"):
+                    c = int(v)
+                    vals.append(math.log(c) if c > 0 else -math.inf)
+                else:
+                    vals.append(float(v))
+            return vals
+    return None
+
+
+def run_full(args, wl):
+    """Time to solution: init, then rounds until every window has ln f < ln f_final."""
+    import numpy as np
+    import torch
+    import paper_1402_2328_gb300.rewl as R
+
+    torch.cuda.set_device(0)
+    r = R.REWL(wl["model"], wl["L"], wl["windows"], wl["overlap"], wl["walkers"], wl["lnf_final"],
+               wl["flatness"], seed=seed_for(wl["config_id"]), interval=wl["interval"],
+               lnf_init=args.lnf_init)
+    t0 = time.perf_counter()
+    r.init()
+    t_init = time.perf_counter() - t0
+    status = r.run(max_seconds=args.max_seconds)
+    t_run = time.perf_counter() - t0 - t_init
+    st = r.stats()
+    out = {"workload": args.workload, "status": status, "seconds_init": t_init,
+           "seconds_run": t_run, "rounds": st["rounds"], "attempts": st["attempts"],
+           "attempts_per_s": st["attempts"] / max(t_run, 1e-9),
+           "windows_finished": st["windows_finished"], "windows": r.h,
+           "min_iteration": st["min_iteration"], "max_lnf": st["max_lnf"],
+           "swap_acceptance": st["swap_accepted"] / max(st["swap_attempts"], 1),
+           "exact_fraction": st["exact_decisions"] / max(st["attempts"], 1)}
+    if status == "done":
+        lng, joins = r.stitch(0)
+        ex = exact_lng_golden(wl["model"], wl["L"])
+        if ex is not None:
+            ex = np.array(ex)
+            fin = np.isfinite(ex)
+            mx = ex[fin].max()
+            ex = ex - (mx + math.log(np.exp(ex[fin] - mx).sum()) - r.N * math.log(2))
+            out["max_abs_dlng_vs_exact"] = float(np.max(np.abs(lng[fin] - ex[fin])))
+            out["rms_dlng_vs_exact"] = float(np.sqrt(np.mean((lng[fin] - ex[fin]) ** 2)))
+    r.close()
+    return out
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     import paper_1402_2328_gb300.rewl as R
@@ -352,6 +411,9 @@ def main():
     ap.add_argument("--cpu-rounds", type=int, default=2, help="oracle rounds per core (baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lnf-init", type=float, default=1.0, help="ln f of the first iteration")
+    ap.add_argument("--full-run", action="store_true",
+                    help="run the workload to ln f < ln f_final and report the time to solution")
+    ap.add_argument("--max-seconds", type=float, default=1800.0, help="cap of --full-run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -359,6 +421,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     procs = os.cpu_count() or 1
+
+    if args.full_run:
+        print(json.dumps({"full_run": run_full(args, wl)}))
+        return
 
     if args.impl == "reference":
         # the oracle is the reference arm: rank 0 only, host cores only

@@ -13,7 +13,7 @@
  *   - A handle owns its device state (cudaMalloc'd in rewl_create, freed in rewl_destroy)
  *     and enqueues all work on the stream given by rewl_set_stream (default: the legacy
  *     default stream).  A handle is not thread safe.
- *   - Lattices: 2 <= L <= 255 and the move kernel's shared memory (5 bytes per site plus
+ *   - Lattices: 2 <= L <= 255 and the move kernel's shared memory (3 bytes per site plus
  *     12 bytes per window bin) must fit one CTA.
  *   - Models: model = 0 is the 2D Ising model E = -sum_<ij> s_i s_j (J = 1, s = +-1);
  *     model = q >= 2 is the q-state Potts model E = -sum_<ij> delta(s_i, s_j).  L x L
@@ -72,7 +72,11 @@ int rewl_create(rewl_t *out, int model, int L, int windows, double overlap,
  * stream, default 0), "graph_rounds" (rounds per CUDA-graph replay, default 32; 0 = no
  * graph), "walkers_per_block" (warps per CTA of the move kernel; 0 = automatic),
  * "check_all" (1 = decide every move with the float64 path as well and count
- * disagreements; diagnostic), "profile" (1 = time move-kernel launches with CUDA events,
+ * disagreements; diagnostic), "schedule" (0 = ln f halving, f -> sqrt f, Sec. 2; 1 = the "1/t
+ * algorithm" the paper names as an alternative: after a halving, once ln f < 1/t with
+ * t = moves per walker / visited bins of the window, ln f = 1/t is recomputed at every check,
+ * where the m walkers' ln g are averaged, without a flatness test), "profile" (1 = time
+ * move-kernel launches with CUDA events,
  * see rewl_kernel_time; may be changed at any time).  Unknown key or bad value: INVALID_ARG.
  */
 int rewl_set_param(rewl_t r, const char *key, double value);
@@ -93,6 +97,22 @@ int rewl_set_lng_init(rewl_t r, const double *lng_bins, int n);
  * Used for run-time balanced splitting (Fig. 1b) and learned window boundaries.
  */
 int rewl_set_windows(rewl_t r, const int *lo_hi, int h);
+
+/*
+ * rewl_windows_balanced -- run-time balanced windows (Fig. 1b).  host cost[B+1] >= 0 is the
+ * expected first-iteration work per bin; the h windows are the equal-size layout with overlap
+ * `overlap` placed in the coordinate u(b) = (cumulative cost up to b) / (total cost), so every
+ * window carries the same share of work (each kept >= 5 bins wide and overlapping the next).
+ * Uniform cost gives the equal-size layout.  lo_hi: host, 2h ints (lo[], then hi[]).  Host only.
+ */
+int rewl_windows_balanced(const double *cost, int B, int h, double overlap, int *lo_hi);
+/*
+ * rewl_balanced_from_prerun -- the cost profile of a short pre-run with equal windows, after
+ * every window finished its first iteration (field "first_iter_round" > 0): a bin's cost is the
+ * mean, over the windows covering it, of (first-iteration rounds) / (window width); then
+ * rewl_windows_balanced with h windows.  Use the result with rewl_set_windows on a new handle.
+ */
+int rewl_balanced_from_prerun(rewl_t pre, int h, double overlap, int *lo_hi);
 
 /* rewl_set_stream -- cudaStream_t (as void*) for all later work of this handle. */
 int rewl_set_stream(rewl_t r, void *stream);
@@ -155,6 +175,15 @@ int rewl_get_lng(rewl_t r, int window, int walker, double *out, int cap, int *lo
 int rewl_stitch(rewl_t r, double *out, int cap, int norm, int *joins);
 
 /*
+ * rewl_jackknife -- statistical error of the joined ln g from the m walkers' fragments
+ * (Sec. 3: "standard resampling techniques"): each walker's ln g just before its window's last
+ * averaging is kept; for j = 1..m the windows' means without walker j are joined as in
+ * rewl_stitch (same norm), and err[b] = sqrt((m-1)/m * sum_j (theta_j[b] - mean)^2), NaN where a
+ * resample has no value.  Needs m >= 2 and every window finished.  err: host, cap >= B+1.
+ */
+int rewl_jackknife(rewl_t r, double *err, int cap, int norm);
+
+/*
  * rewl_dims -- out (host, 8 ints): N, B, windows, walkers per window, W (row stride of
  * per-walker ln g / H arrays = widest window), q, L, model.
  */
@@ -170,7 +199,10 @@ int rewl_dims(rewl_t r, int *out);
  *   uint64[h], "swap_acc" uint64[h] (pair (w,w+1) at index w), "pstep" uint64[nw],
  *   "prep_restarts" int32[nw], "round" int64[1], "lo" int32[h], "hi" int32[h],
  *   "n_exact" uint64[1] (moves decided by the float64 path), "n_mismatch" uint64[1],
- *   "lng_mean" float64[h][W] (window means of ln g, walker order; computed on the GPU).
+ *   "lng_mean" float64[h][W] (window means of ln g, walker order; computed on the GPU),
+ *   "first_iter_round" int64[h] (rounds done when the window's first iteration ended, 0 if
+ *   not yet: times `interval` it is the MC steps of Eq. (5)), "mode" uint8[h] (1: 1/t),
+ *   "frag" float64[nw][W] (each walker's ln g just before its window's last averaging).
  * rewl_set_state accepts "spins", "k", "lng", "H", "step" (tests plant states with it).
  */
 int rewl_get_state(rewl_t r, const char *field, void *out, size_t bytes);
@@ -268,6 +300,50 @@ const char *rewl_batch_last_error(rewl_batch_t b);
 int rewl_replay(int model, int L, int n, int W, int T, void *spins, void *k, const void *lo,
                 const void *hi, void *lng, void *H, const void *lnf, const void *frozen,
                 const void *words, void *acc, void *dk, void *stream);
+
+/*
+ * Learned warm start.  A 3 -> 64 -> 64 -> 1 MLP (tanh, float32 weights) maps the features
+ * (e = E/N in the Potts convention -- Ising energies mapped by E_P = (E_I - 2N)/2 --, q, 1/L)
+ * of an energy bin to ln g(E)/N (g normalised to sum q^N).  It is trained on converged ln g of
+ * small lattices and predicts a warm-start ln g for a larger one (rewl_set_lng_init); the run
+ * then starts from a small ln f.  The paper has no counterpart; plain cold-start REWL stays the
+ * fallback and the judge of its error.  All pointers are device pointers; stream may be NULL.
+ * Parameter vector P (REWL_MLP_NPARAM floats): W1[64][3], b1[64], W2[64][64] (W2[i][j]: from
+ * hidden-1 unit j to hidden-2 unit i), b2[64], W3[64], b3.  X: n x 3 features, T: n targets.
+ */
+#define REWL_MLP_NPARAM 4481
+/* Y[i] = net(X[i]). */
+int rewl_mlp_forward(const float *P, const float *X, float *Y, int n, void *stream);
+/* floats of workspace rewl_mlp_grad / rewl_mlp_train need for n samples */
+int rewl_mlp_workspace_floats(int n);
+/* grad = d/dP of mean_i (net(X_i) - T_i)^2 (back-propagation; sums in sample order, so the
+ * result does not depend on scheduling); *loss (device, may be NULL) = that mean. */
+int rewl_mlp_grad(const float *P, const float *X, const float *T, int n, float *grad, float *loss,
+                  float *work, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; t >= 1) on P with state m, v. */
+int rewl_mlp_adam(float *P, const float *grad, float *m, float *v, int t, double lr, void *stream);
+/* `steps` full-batch Adam steps (step numbers t0+1 ...); loss_out (may be NULL) gets the loss
+ * before the last step.  grad: NPARAM floats; work: rewl_mlp_workspace_floats(n) floats. */
+int rewl_mlp_train(float *P, const float *X, const float *T, int n, int steps, double lr, int t0,
+                   float *m, float *v, float *grad, float *work, float *loss_out, void *stream);
+/* Glorot-uniform weights from Philox4x32-10 keyed by seed, zero biases. */
+int rewl_mlp_init(float *P, uint64_t seed, void *stream);
+/* Training samples of one converged ln g (B+1 float64 values, -INFINITY = unvisited): one per
+ * visited bin, in bin order, written to X (3 floats each) and T; *count (device int) = number. */
+int rewl_mlp_samples(const double *lng, int model, int L, float *X, float *T, int *count,
+                     void *stream);
+/* lng[b] = N * net(e_b, q, 1/L) for the B+1 bins of lattice (model, L), float64. */
+int rewl_mlp_predict(const float *P, int model, int L, double *lng, void *stream);
+const char *rewl_mlp_last_error(void);
+
+/*
+ * rewl_thermo -- canonical averages from a density of states (Eqs. 6-7), k_B = 1: for each
+ * temperature T[i], U[i] = <E>/N and C[i] = (<E^2> - <E>^2) / (N T[i]^2), the averages weighted
+ * by g(E) e^{-E/T}.  lng: device, B+1 float64 (-INFINITY = unreachable bin); T, U, C: device,
+ * nT float64.  Bin energies: Ising E = -2N + 4k, Potts E = -2N + k.
+ */
+int rewl_thermo(const double *lng, int model, int L, const double *T, int nT, double *U, double *C,
+                void *stream);
 
 /*
  * rewl_replay_static -- rewl_replay that allocates nothing.  The paper has no counterpart:

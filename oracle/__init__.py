@@ -63,6 +63,8 @@ def lib():
         L.or_rewl_get.argtypes = [P] * 17
         L.or_rewl_put.argtypes = [P] * 6
         L.or_rewl_window_mean.argtypes = [P, C.c_int, P]
+        L.or_rewl_set_schedule.argtypes = [P, C.c_int]
+        L.or_rewl_get_extra.argtypes = [P, P, P, P]
         L.or_stitch.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, C.c_double, C.c_int,
                                 C.c_int, C.c_double, P, P]
         _lib = L
@@ -128,7 +130,7 @@ class REWL:
     def __init__(self, model: int, L: int, windows: int, overlap: float, walkers: int,
                  lnf_final: float, flatness: float, seed: int, instance: int = 0,
                  interval: int = 10_000, prep_budget: int = 100, lnf_init: float = 1.0,
-                 lng_init=None):
+                 lng_init=None, schedule: int = 0):
         self._lib = lib()
         self._h = self._lib.or_rewl_create(model, L, windows, overlap, walkers, lnf_final,
                                            flatness, seed, instance, interval, prep_budget,
@@ -143,6 +145,7 @@ class REWL:
         self.lo = np.zeros(self.h, dtype=np.int32)
         self.hi = np.zeros(self.h, dtype=np.int32)
         self._lib.or_rewl_windows_get(self._h, _p(self.lo), _p(self.hi))
+        self._lib.or_rewl_set_schedule(self._h, schedule)
         if lng_init is not None:
             g = np.ascontiguousarray(lng_init, dtype=np.float64)
             assert g.shape == (self.B + 1,)
@@ -180,6 +183,11 @@ class REWL:
                  "swap_att", "swap_acc", "pstep", "prep_restarts"]
         self._lib.or_rewl_get(self._h, *[_p(s[o]) for o in order], C.byref(rd))
         s["round"] = rd.value
+        s["first_iter_round"] = np.zeros(h, np.int64)
+        s["mode"] = np.zeros(h, np.uint8)
+        s["frag"] = np.zeros((nw, W), np.float64)
+        self._lib.or_rewl_get_extra(self._h, _p(s["first_iter_round"]), _p(s["mode"]),
+                                    _p(s["frag"]))
         return s
 
     def put(self, spins=None, k=None, lng=None, H=None, step=None):
@@ -192,6 +200,28 @@ class REWL:
         out = np.zeros(int(self.hi[w] - self.lo[w] + 1), dtype=np.float64)
         self._lib.or_rewl_window_mean(self._h, w, _p(out))
         return out
+
+    def jackknife(self, norm: int = 0):
+        """Per-bin jackknife error of the joined ln g over the m walker fragments (Sec. 3)."""
+        st = self.state()
+        m, W = self.m, self.W
+        thetas = []
+        for j in range(m):
+            lngw = np.zeros((self.h, W), np.float64)
+            for w in range(self.h):
+                nb = int(self.hi[w] - self.lo[w] + 1)
+                acc = np.zeros(nb)
+                for i in range(m):
+                    if i != j:
+                        acc = acc + st["frag"][w * m + i, :nb]
+                lngw[w, :nb] = acc / (m - 1)
+            thetas.append(stitch(self.model, self.L, self.lo, self.hi, lngw, st["mask"], norm)[0])
+        th = np.array(thetas)
+        fin = np.all(np.isfinite(th), axis=0)
+        err = np.full(th.shape[1], np.nan)
+        mean = th[:, fin].mean(axis=0)
+        err[fin] = np.sqrt((m - 1) / m * ((th[:, fin] - mean) ** 2).sum(axis=0))
+        return err
 
     def stitch(self, norm: int = 0):
         """Joined ln g over the B+1 bins (Sec. 3, Eq. 2) from the window means."""

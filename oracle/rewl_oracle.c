@@ -42,6 +42,10 @@
  *           m partners; ln P = (lg_i[kX]-lg_i[kY]) + (lg_j[kY]-lg_j[kX]).
  *   prep:   from the seeded random state, accept a move iff the distance of k to the window
  *           does not grow; after prep_budget sweeps restart from the ordered state.
+ *   1/t:    (optional schedule, Sec. 2 names the "1/t algorithm" as a valid alternative) after a
+ *           halving, if ln f < 1/t with t = (moves per walker) / (visited bins of the window),
+ *           the window switches to ln f = 1/t, recomputed at every check, where the m walkers'
+ *           ln g are averaged as at an advance, with no flatness test.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fast-math; explicit fma only).
  */
@@ -286,6 +290,10 @@ typedef struct {
     uint8_t *finished;  /* [h] */
     uint8_t *mask;      /* [h][W] bins visited by any walker of the window */
     uint64_t *swap_att, *swap_acc; /* [h] (index w = pair (w,w+1)) */
+    long long *it1_round;  /* [h] rounds done when the first iteration ended (0: not yet) */
+    double *frag;          /* [nw][W] each walker's ln g just before its window's last average */
+    uint8_t *mode;         /* [h] 0: halving, 1: ln f = 1/t */
+    int schedule;          /* 0: f -> sqrt f only, 1: switch to 1/t */
     long long round;
 } or_rewl;
 
@@ -297,7 +305,7 @@ void or_rewl_destroy(or_rewl *r)
     free(r->lo); free(r->hi); free(r->spins); free(r->k); free(r->lng); free(r->H);
     free(r->step); free(r->acc); free(r->pstep); free(r->prep_restarts); free(r->flat);
     free(r->lnf); free(r->iter); free(r->finished); free(r->mask);
-    free(r->swap_att); free(r->swap_acc);
+    free(r->swap_att); free(r->swap_acc); free(r->it1_round); free(r->mode); free(r->frag);
     free(r);
 }
 
@@ -346,6 +354,9 @@ or_rewl *or_rewl_create(int model, int L, int h, double overlap, int m, double l
     r->mask = (uint8_t *)zalloc((size_t)h * W);
     r->swap_att = (uint64_t *)zalloc(8 * (size_t)h);
     r->swap_acc = (uint64_t *)zalloc(8 * (size_t)h);
+    r->it1_round = (long long *)zalloc(8 * (size_t)h);
+    r->frag = (double *)zalloc(sizeof(double) * nw * W);
+    r->mode = (uint8_t *)zalloc(h);
     for (int w = 0; w < h; w++) {
         r->lnf[w] = lnf_init;
         r->finished[w] = lnf_init < lnf_final;
@@ -424,7 +435,9 @@ static void check_window(or_rewl *r, int w)
             if (H[b] > 0) mask[b] = 1;
     }
     int all = 1;
-    for (int i = 0; i < m; i++) {
+    long long nvis = 0;
+    for (int b = 0; b < nb; b++) nvis += mask[b];
+    for (int i = 0; i < m && !r->mode[w]; i++) {
         int g = w * m + i;
         if (!r->flat[g]) {
             const uint32_t *H = r->H + (size_t)g * W;
@@ -441,7 +454,16 @@ static void check_window(or_rewl *r, int w)
         }
         all &= r->flat[g];
     }
-    if (!all) return;
+    if (!all) return; /* in 1/t mode no walker is ever flagged flat: all stays 1 */
+    /* ln f after this advance (same arithmetic as below): a window about to finish keeps its
+       walkers' last fragments for resampling error bars (Sec. 3) */
+    double inv_t0 = nvis > 0 ? (double)nvis / (double)r->step[w * m] : 0.0;
+    double nl0 = r->mode[w] ? inv_t0 : r->lnf[w] * 0.5;
+    if (!r->mode[w] && r->schedule == 1 && nl0 < inv_t0) nl0 = inv_t0;
+    if (nl0 < r->lnf_final)
+        for (int i = 0; i < m; i++)
+            memcpy(r->frag + (size_t)(w * m + i) * W, r->lng + (size_t)(w * m + i) * W,
+                   sizeof(double) * (size_t)nb);
     for (int b = 0; b < nb; b++) {
         double acc = 0.0;
         for (int i = 0; i < m; i++) acc = acc + r->lng[(size_t)(w * m + i) * W + b];
@@ -452,9 +474,28 @@ static void check_window(or_rewl *r, int w)
         }
     }
     for (int i = 0; i < m; i++) r->flat[w * m + i] = 0;
-    r->lnf[w] = r->lnf[w] * 0.5;
+    /* 1/t with t = moves per walker / visited bins, i.e. ln f = visited bins / moves */
+    double inv_t = nvis > 0 ? (double)nvis / (double)r->step[w * m] : 0.0;
+    if (r->mode[w]) {
+        r->lnf[w] = inv_t;
+    } else {
+        r->lnf[w] = r->lnf[w] * 0.5;
+        if (r->schedule == 1 && r->lnf[w] < inv_t) {
+            r->mode[w] = 1;
+            r->lnf[w] = inv_t;
+        }
+    }
+    if (r->iter[w] == 0) r->it1_round[w] = r->round + 1;
     r->iter[w] += 1;
     if (r->lnf[w] < r->lnf_final) r->finished[w] = 1;
+}
+
+void or_rewl_set_schedule(or_rewl *r, int schedule) { r->schedule = schedule; }
+void or_rewl_get_extra(const or_rewl *r, long long *it1_round, uint8_t *mode, double *frag)
+{
+    if (it1_round) memcpy(it1_round, r->it1_round, 8 * (size_t)r->h);
+    if (mode) memcpy(mode, r->mode, (size_t)r->h);
+    if (frag) memcpy(frag, r->frag, sizeof(double) * (size_t)r->nw * r->W);
 }
 
 /* Replica exchange between windows w and w+1 in round rd (Sec. 2, Eq. 1). */

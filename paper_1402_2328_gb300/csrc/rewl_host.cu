@@ -95,7 +95,7 @@ static void release(rewl_t r)
     State &s = r->st;
     void *ptrs[] = {s.spins, s.cfg, s.k, s.lng, s.H, s.step, s.acc, s.pstep, s.restarts, s.flat,
                     r->d_lohi, s.lnf, s.iter, s.finished, s.mask, s.swap_att, s.swap_acc,
-                    s.status, r->d_mean, r->d_out, r->d_joins, r->d_ok};
+                    s.it1_round, s.mode, s.frag, s.status, r->d_mean, r->d_out, r->d_joins, r->d_ok};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (r->h_status) cudaFreeHost(r->h_status);
@@ -147,6 +147,9 @@ static int allocate(rewl_t r)
     s.mask = dmalloc<uint8_t>(h * W, e);
     s.swap_att = dmalloc<unsigned long long>(h, e);
     s.swap_acc = dmalloc<unsigned long long>(h, e);
+    s.it1_round = dmalloc<long long>(h, e);
+    s.mode = dmalloc<uint8_t>(h, e);
+    s.frag = dmalloc<double>(nw * W, e);
     s.status = dmalloc<DevStatus>(1, e);
     r->d_mean = dmalloc<double>(h * W, e);
     r->d_out = dmalloc<double>((size_t)r->B + 1, e);
@@ -230,6 +233,7 @@ int rewl_set_param(rewl_t r, const char *key, double v)
     else if (k == "graph_rounds" && v >= 0 && v <= 4096) r->graph_rounds = (int)v;
     else if (k == "walkers_per_block" && v >= 0 && v <= 16) r->wpb = (int)v;
     else if (k == "check_all" && (v == 0 || v == 1)) r->check_all = (int)v;
+    else if (k == "schedule" && (v == 0 || v == 1)) r->schedule = (int)v;
     else return r->fail(REWL_ERR_INVALID_ARG, "rewl_set_param: unknown key or bad value: " + k);
     if (k == "instance") r->st.inst = r->inst;
     return REWL_OK;
@@ -322,6 +326,10 @@ int rewl_init(rewl_t r)
     if (e == cudaSuccess) e = cudaMemsetAsync(s.mask, 0, h * W, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.swap_att, 0, h * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.swap_acc, 0, h * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.it1_round, 0, h * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.mode, 0, h, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.frag, 0, nw * W * 8, st);
+    s.schedule = r->schedule;
     if (e == cudaSuccess) e = cudaMemsetAsync(s.status, 0, sizeof(DevStatus), st);
     if (e == cudaSuccess) e = launch_init_prep(s, r->prep_budget, st);
     if (e == cudaSuccess) e = launch_set_done(s, st);
@@ -501,6 +509,125 @@ int rewl_abort(rewl_t r)
     return REWL_OK;
 }
 
+int rewl_jackknife(rewl_t r, double *err, int cap, int norm)
+{
+    if (!r || !err || (norm != 0 && norm != 1)) return REWL_ERR_INVALID_ARG;
+    if (cap < r->B + 1) return r->fail(REWL_ERR_BUFFER_TOO_SMALL, "rewl_jackknife: cap < B+1");
+    if (r->m < 2) return r->fail(REWL_ERR_STATE, "rewl_jackknife: needs at least 2 walkers per window");
+    std::vector<uint8_t> fin((size_t)r->h);
+    int rc = rewl_get_state(r, "finished", fin.data(), fin.size());
+    if (rc != REWL_OK) return rc;
+    for (uint8_t f : fin)
+        if (!f) return r->fail(REWL_ERR_STATE, "rewl_jackknife: every window must be finished");
+    const double de = r->model == 0 ? 4.0 : 1.0;
+    const int step = (r->model != 0 && r->q == 2) ? 2 : 1;
+    const double target = norm == 0 ? (double)r->N * std::log((double)r->q) : std::log((double)r->q);
+    double *theta = nullptr, *d_err = nullptr;
+    cudaError_t e = cudaMalloc(&theta, (size_t)r->m * (r->B + 1) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_err, (size_t)(r->B + 1) * 8);
+    std::vector<int> oks((size_t)r->m, 0);
+    for (int j = 0; j < r->m && e == cudaSuccess; ++j) {
+        e = launch_loo_mean(r->st, j, r->d_mean, r->stream);
+        if (e == cudaSuccess)
+            e = launch_stitch(r->st, r->d_mean, de, step, norm, target, theta + (size_t)j * (r->B + 1),
+                              r->d_joins, r->d_ok, r->B, r->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&oks[j], r->d_ok, sizeof(int), cudaMemcpyDeviceToHost, r->stream);
+    }
+    if (e == cudaSuccess) e = launch_jack(theta, r->m, r->B, d_err, r->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(err, d_err, (size_t)(r->B + 1) * 8, cudaMemcpyDeviceToHost, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    cudaFree(theta);
+    cudaFree(d_err);
+    if (e != cudaSuccess) return r->cuda_fail(e, "rewl_jackknife");
+    for (int ok : oks)
+        if (!ok) return r->fail(REWL_ERR_NOT_CONVERGED, "rewl_jackknife: a resample cannot be joined");
+    return REWL_OK;
+}
+
+int rewl_windows_balanced(const double *cost, int B, int h, double overlap, int *lo_hi)
+{
+    if (!cost || !lo_hi || B < 1 || h < 1 || !(overlap >= 0.0 && overlap < 1.0)) {
+        g_err = "rewl_windows_balanced: invalid argument";
+        return REWL_ERR_INVALID_ARG;
+    }
+    // cumulative cost C(b) = sum_{x < b} cost[x] + (cost of b)/2, then equal-size windows with
+    // overlap o in the coordinate u = C / C_total (Fig. 1b: run-time balanced subdivision)
+    std::vector<double> cum(B + 2, 0.0);
+    for (int b = 0; b <= B; ++b) {
+        if (!(cost[b] >= 0.0) || !std::isfinite(cost[b])) {
+            g_err = "rewl_windows_balanced: cost must be finite and >= 0";
+            return REWL_ERR_INVALID_ARG;
+        }
+        cum[b + 1] = cum[b] + cost[b];
+    }
+    const double tot = cum[B + 1];
+    std::vector<int> lo(h), hi(h);
+    if (h == 1 || !(tot > 0.0)) {
+        if (make_windows(B, h, overlap, lo, hi) != 0) {
+            g_err = "rewl_windows_balanced: windows do not overlap";
+            return REWL_ERR_INVALID_ARG;
+        }
+    } else {
+        const double W = 1.0 / (1.0 + (double)(h - 1) * (1.0 - overlap));
+        const double st = (1.0 - overlap) * W;
+        auto bin_at = [&](double u) { // first bin whose cumulative cost reaches u * tot
+            const double target = u * tot;
+            int a = 0, z = B;
+            while (a < z) {
+                const int mid = (a + z) / 2;
+                if (cum[mid + 1] >= target) z = mid;
+                else a = mid + 1;
+            }
+            return a;
+        };
+        for (int k = 0; k < h; ++k) {
+            lo[k] = k == 0 ? 0 : bin_at((double)k * st);
+            hi[k] = k == h - 1 ? B : bin_at((double)k * st + W);
+        }
+        // keep every window at least 5 bins wide and strictly overlapping its successor
+        for (int k = 0; k < h; ++k) {
+            if (k > 0 && lo[k] <= lo[k - 1]) lo[k] = lo[k - 1] + 1;
+            if (hi[k] < lo[k] + 4) hi[k] = std::min(B, lo[k] + 4);
+            if (k > 0 && hi[k] <= hi[k - 1]) hi[k] = std::min(B, hi[k - 1] + 1);
+        }
+        hi[h - 1] = B;
+        for (int k = 0; k + 1 < h; ++k)
+            if (lo[k + 1] > hi[k] - 1) lo[k + 1] = std::max(lo[k] + 1, hi[k] - 1);
+        if (check_windows(B, lo, hi) != 0) {
+            g_err = "rewl_windows_balanced: too many windows for this cost profile";
+            return REWL_ERR_INVALID_ARG;
+        }
+    }
+    for (int k = 0; k < h; ++k) {
+        lo_hi[k] = lo[k];
+        lo_hi[h + k] = hi[k];
+    }
+    return REWL_OK;
+}
+
+int rewl_balanced_from_prerun(rewl_t pre, int h, double overlap, int *lo_hi)
+{
+    if (!pre || !lo_hi || h < 1) return REWL_ERR_INVALID_ARG;
+    std::vector<long long> t1((size_t)pre->h);
+    int rc = rewl_get_state(pre, "first_iter_round", t1.data(), t1.size() * 8);
+    if (rc != REWL_OK) return rc;
+    for (long long v : t1)
+        if (v <= 0) return pre->fail(REWL_ERR_STATE, "pre-run: a window has not finished its first iteration");
+    // per-bin cost density: mean over the windows covering the bin of t_w / width_w
+    std::vector<double> c((size_t)pre->B + 1, 0.0), n((size_t)pre->B + 1, 0.0);
+    for (int w = 0; w < pre->h; ++w) {
+        const double d = (double)t1[w] / (double)(pre->hi[w] - pre->lo[w] + 1);
+        for (int b = pre->lo[w]; b <= pre->hi[w]; ++b) {
+            c[b] += d;
+            n[b] += 1.0;
+        }
+    }
+    for (int b = 0; b <= pre->B; ++b) c[b] = n[b] > 0 ? c[b] / n[b] : 0.0;
+    rc = rewl_windows_balanced(c.data(), pre->B, h, overlap, lo_hi);
+    if (rc != REWL_OK) return pre->fail(rc, g_err);
+    return REWL_OK;
+}
+
 int rewl_dims(rewl_t r, int *out)
 {
     if (!r || !out) return REWL_ERR_INVALID_ARG;
@@ -585,6 +712,9 @@ static bool field(rewl_t r, const std::string &f, Field &out)
     else if (f == "swap_acc") out = {s.swap_acc, h * 8, false};
     else if (f == "pstep") out = {s.pstep, nw * 8, false};
     else if (f == "prep_restarts") out = {s.restarts, nw * 4, false};
+    else if (f == "first_iter_round") out = {s.it1_round, h * 8, false};
+    else if (f == "mode") out = {s.mode, h, false};
+    else if (f == "frag") out = {s.frag, nw * W * 8, false};
     else if (f == "lo") out = {r->d_lohi, h * 4, false};
     else if (f == "hi") out = {r->d_lohi + h, h * 4, false};
     else return false;
@@ -723,7 +853,8 @@ static std::vector<Field> ckpt_fields(rewl_t r)
             {s.acc, nw * 8, true},              {s.pstep, nw * 8, true}, {s.restarts, nw * 4, true},
             {s.flat, nw, true},                 {r->d_lohi, 2 * h * 4, true}, {s.lnf, h * 8, true},
             {s.iter, h * 4, true},              {s.finished, h, true},   {s.mask, h * W, true},
-            {s.swap_att, h * 8, true},          {s.swap_acc, h * 8, true}, {s.status, sizeof(DevStatus), true}};
+            {s.swap_att, h * 8, true},          {s.swap_acc, h * 8, true}, {s.status, sizeof(DevStatus), true},
+            {s.it1_round, h * 8, true},         {s.mode, h, true}, {s.frag, nw * W * 8, true}};
 }
 
 int rewl_checkpoint(rewl_t r, const char *path)
@@ -1055,6 +1186,21 @@ int rewl_lnu_bound(uint64_t begin, uint64_t end, double *max_err, unsigned long 
 }
 
 double rewl_lnu_eps(void) { return LNU32_EPS; }
+
+int rewl_thermo(const double *lng, int model, int L, const double *T, int nT, double *U, double *C,
+                void *stream)
+{
+    if (!lng || !T || !U || !C || nT < 0 || L < 2 || (model != 0 && model < 2)) {
+        g_err = "rewl_thermo: invalid argument";
+        return REWL_ERR_INVALID_ARG;
+    }
+    cudaError_t e = launch_thermo(lng, model, L, T, nT, U, C, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        g_err = cudaGetErrorString(e);
+        return REWL_ERR_CUDA;
+    }
+    return REWL_OK;
+}
 
 int rewl_seqadd(const double *x, const double *f, const uint32_t *c, double *out, int n, void *stream)
 {

@@ -127,7 +127,7 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
     int8_t *sp = reinterpret_cast<int8_t *>(base);
     long long *V = reinterpret_cast<long long *>(base + pad16(s.N));
     uint32_t *Hs = reinterpret_cast<uint32_t *>(V + padw(s.W));
-    unsigned *stamp = reinterpret_cast<unsigned *>(Hs + padw(s.W)); // [N] batch claims
+    uint16_t *stamp = reinterpret_cast<uint16_t *>(Hs + padw(s.W)); // [N] batch claims
 
     const int w = slot / s.m;
     const int lo = s.lo[w], hi = s.hi[w], nb = hi - lo + 1;
@@ -153,7 +153,7 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
     } else {
         for (int i = lane; i < s.N; i += 32) sp[i] = gsp[i];
     }
-    for (int i = lane; i < s.N; i += 32) stamp[i] = 0u;
+    for (int i = lane; i < s.N; i += 32) stamp[i] = 0xffffu; // matches no batch
     double mx = 0.0;
     bool bad = false;
     for (int b = lane; b < nb; b += 32) {
@@ -227,8 +227,11 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         const float thr = lnu32(w2);
         // conflict-free prefix: proposal j may be resolved on the batch-start lattice only if
         // no earlier proposal of the batch sits on its site or a neighbour
-        const unsigned claim = (batch << 5) | (unsigned)(31 - lane);
-        if (lane < n) atomicMax(&stamp[site], claim);
+        // claim stamp = (batch mod 2047) << 5 | lane, written by the lowest lane proposing the site;
+        // a stale stamp of an old batch with the same low bits can only cut a batch early
+        const unsigned btag = batch % 2047u;
+        const unsigned peers = __match_any_sync(FULL, lane < n ? site : -1 - lane);
+        if (lane < n && lane == __ffs(peers) - 1) stamp[site] = (uint16_t)((btag << 5) | (unsigned)lane);
         __syncwarp();
         bool conflict = false;
         {
@@ -236,7 +239,7 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
                 const unsigned v = stamp[xs[m]];
-                conflict = conflict || ((v >> 5) == batch && (31 - (int)(v & 31u)) < lane);
+                conflict = conflict || ((v >> 5) == btag && (int)(v & 31u) < lane);
             }
         }
         const unsigned cmask = __ballot_sync(FULL, conflict && lane < n);
@@ -554,7 +557,15 @@ __device__ __forceinline__ void check_window(const State &s, const int w, const 
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int i = wid; i < m; i += nwarp) {
+    // visited bins of the window (for t of the 1/t schedule)
+    __shared__ int nvis_w[32];
+    int nv = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) nv += mask[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(FULL, nv, o);
+    if (lane == 0) nvis_w[wid] = nv;
+    const bool tmode = s.mode[w] != 0;
+    for (int i = wid; i < m && !tmode; i += nwarp) {
         const int g = w * m + i;
         if (s.flat[g]) continue;
         const uint32_t *H = s.H + (size_t)g * W;
@@ -582,16 +593,35 @@ __device__ __forceinline__ void check_window(const State &s, const int w, const 
     __shared__ int all;
     if (threadIdx.x == 0) {
         int a = 1;
-        for (int i = 0; i < m; ++i) a &= s.flat[w * m + i];
-        all = a;
+        for (int i = 0; i < m && !tmode; ++i) a &= s.flat[w * m + i];
+        all = a; // 1/t mode: every check averages and sets ln f = 1/t
     }
     __syncthreads();
     if (!all) return;
+    // ln f after this advance (every thread computes the same value)
+    long long nvis = 0;
+    for (int i = 0; i < nwarp; ++i) nvis += nvis_w[i];
+    // 1/t with t = moves per walker / visited bins, i.e. ln f = visited bins / moves
+    const double inv_t = nvis > 0 ? __ddiv_rn((double)nvis, (double)s.step[w * m]) : 0.0;
+    bool to_t = false;
+    double nl;
+    if (tmode) {
+        nl = inv_t;
+    } else {
+        nl = __dmul_rn(s.lnf[w], 0.5);
+        if (s.schedule == 1 && nl < inv_t) {
+            to_t = true;
+            nl = inv_t;
+        }
+    }
+    // a window about to finish keeps its walkers' last fragments (resampling error bars, Sec. 3)
+    const bool finishing = nl < lnf_final;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         double acc = 0.0;
         for (int i = 0; i < m; ++i) acc = __dadd_rn(acc, s.lng[(size_t)(w * m + i) * W + b]);
         const double avg = __ddiv_rn(acc, (double)m);
         for (int i = 0; i < m; ++i) {
+            if (finishing) s.frag[(size_t)(w * m + i) * W + b] = s.lng[(size_t)(w * m + i) * W + b];
             s.lng[(size_t)(w * m + i) * W + b] = avg;
             s.H[(size_t)(w * m + i) * W + b] = 0u;
         }
@@ -599,10 +629,11 @@ __device__ __forceinline__ void check_window(const State &s, const int w, const 
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 0; i < m; ++i) s.flat[w * m + i] = 0;
-        const double nl = __dmul_rn(s.lnf[w], 0.5);
+        if (to_t) s.mode[w] = 1;
         s.lnf[w] = nl;
+        if (s.iter[w] == 0) s.it1_round[w] = s.status->round + 1;
         s.iter[w] += 1;
-        if (nl < lnf_final) s.finished[w] = 1;
+        if (finishing) s.finished[w] = 1;
     }
 }
 
@@ -1084,6 +1115,114 @@ cudaError_t launch_seqadd(const double *x, const double *f, const uint32_t *c, d
 {
     if (n <= 0) return cudaSuccess;
     k_seqadd<<<(n + 127) / 128, 128, 0, st>>>(x, f, c, out, n);
+    return cudaGetLastError();
+}
+
+} // namespace rewl
+
+namespace rewl {
+
+// ---------------------------------------------------------------------------------------
+// Canonical averages from ln g (Eqs. 6-7): one CTA per temperature; u = <E>/N,
+// c = <(E - <E>)^2> / (N T^2), weights g(E) e^{-E/T} taken relative to their maximum.
+// ---------------------------------------------------------------------------------------
+__global__ void k_thermo(const double *__restrict__ lng, int B, int model, int N,
+                         const double *__restrict__ Ts, double *__restrict__ U,
+                         double *__restrict__ Cv)
+{
+    const double T = Ts[blockIdx.x];
+    auto energy = [&](int b) { return -2.0 * N + (model == 0 ? 4.0 * b : (double)b); };
+    double mx = -INFINITY;
+    for (int b = threadIdx.x; b <= B; b += blockDim.x)
+        if (lng[b] > -INFINITY) mx = fmax(mx, lng[b] - energy(b) / T);
+    mx = block_reduce_max(mx);
+    double s0 = 0.0, s1 = 0.0;
+    for (int b = threadIdx.x; b <= B; b += blockDim.x)
+        if (lng[b] > -INFINITY) {
+            const double w = exp(lng[b] - energy(b) / T - mx);
+            s0 += w;
+            s1 += w * energy(b);
+        }
+    s0 = block_reduce_sum(s0);
+    s1 = block_reduce_sum(s1);
+    const double e1 = s1 / s0;
+    double s2 = 0.0;
+    for (int b = threadIdx.x; b <= B; b += blockDim.x)
+        if (lng[b] > -INFINITY) {
+            const double w = exp(lng[b] - energy(b) / T - mx);
+            const double de = energy(b) - e1;
+            s2 += w * de * de;
+        }
+    s2 = block_reduce_sum(s2);
+    if (threadIdx.x == 0) {
+        U[blockIdx.x] = e1 / N;
+        Cv[blockIdx.x] = s2 / s0 / ((double)N * T * T);
+    }
+}
+
+cudaError_t launch_thermo(const double *lng, int model, int L, const double *T, int nT, double *U,
+                          double *C, cudaStream_t st)
+{
+    if (nT <= 0) return cudaSuccess;
+    const int N = L * L, B = model == 0 ? N : 2 * N;
+    k_thermo<<<nT, 256, 0, st>>>(lng, B, model, N, T, U, C);
+    return cudaGetLastError();
+}
+
+} // namespace rewl
+
+namespace rewl {
+
+// Window means of the saved fragments leaving walker j out (walker order), [h][W].
+__global__ void k_loo_mean(State s, int j, double *out)
+{
+    const int w = blockIdx.x, nb = s.hi[w] - s.lo[w] + 1;
+    for (int b = threadIdx.x; b < s.W; b += blockDim.x) {
+        double v = 0.0;
+        if (b < nb) {
+            double acc = 0.0;
+            for (int i = 0; i < s.m; ++i)
+                if (i != j) acc = __dadd_rn(acc, s.frag[(size_t)(w * s.m + i) * s.W + b]);
+            v = __ddiv_rn(acc, (double)(s.m - 1));
+        }
+        out[(size_t)w * s.W + b] = v;
+    }
+}
+
+cudaError_t launch_loo_mean(const State &s, int j, double *out, cudaStream_t st)
+{
+    k_loo_mean<<<s.h, 256, 0, st>>>(s, j, out);
+    return cudaGetLastError();
+}
+
+// err[b] = sqrt((m-1)/m sum_j (theta_j[b] - mean)^2); NaN where any theta_j is -inf.
+__global__ void k_jack(const double *theta, int m, int B, double *err)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > B) return;
+    double mean = 0.0;
+    bool ok = true;
+    for (int j = 0; j < m; ++j) {
+        const double v = theta[(size_t)j * (B + 1) + b];
+        ok = ok && v > -INFINITY;
+        mean += v;
+    }
+    if (!ok) {
+        err[b] = NAN;
+        return;
+    }
+    mean /= m;
+    double ss = 0.0;
+    for (int j = 0; j < m; ++j) {
+        const double d = theta[(size_t)j * (B + 1) + b] - mean;
+        ss += d * d;
+    }
+    err[b] = sqrt((double)(m - 1) / m * ss);
+}
+
+cudaError_t launch_jack(const double *theta, int m, int B, double *err, cudaStream_t st)
+{
+    k_jack<<<(B + 256) / 256, 256, 0, st>>>(theta, m, B, err);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,10 @@ struct State {
     uint8_t *finished;        // [h]
     uint8_t *mask;            // [h][W]
     unsigned long long *swap_att, *swap_acc; // [h]
+    long long *it1_round;     // [h] rounds done when the first iteration ended (0: not yet)
+    uint8_t *mode;            // [h] 0: ln f halving, 1: ln f = 1/t
+    int schedule;             // 0: halving only, 1: switch to 1/t
+    double *frag;             // [nw][W] ln g of each walker just before its window's last average
     DevStatus *status;
     uint32_t key0, key1, inst;
 };
@@ -53,10 +57,10 @@ struct MoveCfg {
 };
 
 // Shared memory of one walker in the move kernel: lattice (16-byte padded), int64 ln g
-// shadow and uint32 H over the window (padded to 4 bins), uint32 claim stamps per site.
+// shadow and uint32 H over the window (padded to 4 bins), uint16 claim stamps per site.
 __host__ __device__ inline size_t move_smem_per_walker(int N, int W)
 {
-    return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 12u + (size_t)((N + 3) & ~3) * 4u;
+    return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 12u + (size_t)((N + 7) & ~7) * 2u;
 }
 cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st);
 // Batched instances: states/jobs/tables are device arrays (see the kernels).
@@ -76,6 +80,10 @@ cudaError_t launch_stitch(const State &s, const double *mean, double de, int ste
                           double target, double *out /*B+1*/, int *joins /*h-1*/,
                           int *ok /*1*/, int B, cudaStream_t st);
 
+cudaError_t launch_loo_mean(const State &s, int j, double *out /*[h][W]*/, cudaStream_t st);
+cudaError_t launch_jack(const double *theta /*[m][B+1]*/, int m, int B, double *err, cudaStream_t st);
+cudaError_t launch_thermo(const double *lng, int model, int L, const double *T, int nT, double *U,
+                          double *C, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n,
                           cudaStream_t st);
 cudaError_t launch_lnu(const uint32_t *w, double *out, int n, cudaStream_t st);

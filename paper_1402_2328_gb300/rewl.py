@@ -68,6 +68,19 @@ def lib():
             "rewl_lnu_bound": ([C.c_uint64, C.c_uint64, P, P, P], I),
             "rewl_lnu_eps": ([], D),
             "rewl_seqadd": ([P, P, P, P, I, P], I),
+            "rewl_windows_balanced": ([P, I, I, D, P], I),
+            "rewl_thermo": ([P, I, I, P, I, P, P, P], I),
+            "rewl_jackknife": ([P, P, I, I], I),
+            "rewl_balanced_from_prerun": ([P, I, D, P], I),
+            "rewl_mlp_forward": ([P, P, P, I, P], I),
+            "rewl_mlp_workspace_floats": ([I], I),
+            "rewl_mlp_grad": ([P, P, P, I, P, P, P, P], I),
+            "rewl_mlp_adam": ([P, P, P, P, I, D, P], I),
+            "rewl_mlp_train": ([P, P, P, I, I, D, I, P, P, P, P, P, P], I),
+            "rewl_mlp_init": ([P, C.c_uint64, P], I),
+            "rewl_mlp_samples": ([P, I, I, P, P, P, P], I),
+            "rewl_mlp_predict": ([P, I, I, P, P], I),
+            "rewl_mlp_last_error": ([], C.c_char_p),
             "rewl_batch_create": ([P, P, I, C.c_longlong], I),
             "rewl_batch_set_param": ([P, C.c_char_p, D], I),
             "rewl_batch_set_stream": ([P, P], I),
@@ -130,6 +143,7 @@ _FIELDS = {
     "swap_acc": (np.uint64, "h"), "pstep": (np.uint64, "nw"), "prep_restarts": (np.int32, "nw"),
     "round": (np.int64, "1"), "lo": (np.int32, "h"), "hi": (np.int32, "h"),
     "n_exact": (np.uint64, "1"), "n_mismatch": (np.uint64, "1"), "lng_mean": (np.float64, "hW"),
+    "first_iter_round": (np.int64, "h"), "mode": (np.uint8, "h"), "frag": (np.float64, "nwW"),
 }
 
 
@@ -205,6 +219,13 @@ class REWL:
     def set_stream(self, stream=None):
         _check(self._lib.rewl_set_stream(self._h, _stream_ptr(stream)), self._h)
 
+    def balanced_windows(self, h: int, overlap: float = 0.75):
+        """Windows balanced by this (pre-)run's first-iteration times (Fig. 1b)."""
+        a = np.zeros(2 * h, np.int32)
+        _check(self._lib.rewl_balanced_from_prerun(self._h, int(h), float(overlap), _ptr(a)),
+               self._h)
+        return a[:h].copy(), a[h:].copy()
+
     # ---- running
     def init(self):
         _check(self._lib.rewl_init(self._h), self._h)
@@ -240,6 +261,12 @@ class REWL:
         joins = np.zeros(max(self.h - 1, 1), np.int32)
         _check(self._lib.rewl_stitch(self._h, _ptr(out), len(out), norm, _ptr(joins)), self._h)
         return out, joins[: self.h - 1]
+
+    def jackknife(self, norm: int = 0):
+        """Per-bin jackknife error of the joined ln g (NaN where a resample has no value)."""
+        out = np.zeros(self.B + 1, np.float64)
+        _check(self._lib.rewl_jackknife(self._h, _ptr(out), len(out), int(norm)), self._h)
+        return out
 
     def _shape(self, code):
         return {"nwN": (self.nw, self.N), "nw": (self.nw,), "nwW": (self.nw, self.W),
@@ -353,6 +380,65 @@ def replay(model, L, spins, k, lo, hi, lng, H, lnf, frozen, words, acc, dk, stre
     _check(lib().rewl_replay(model, L, n, W, T, _ptr(spins), _ptr(k), _ptr(lo), _ptr(hi),
                              _ptr(lng), _ptr(H), _ptr(lnf), _ptr(frozen), _ptr(words), _ptr(acc),
                              _ptr(dk), _stream_ptr(stream)))
+
+
+def thermo(lng, model, L, T, U, C, stream=None):
+    """u(T) = <E>/N and c(T) from ln g (device tensors)."""
+    _check(lib().rewl_thermo(_ptr(lng), int(model), int(L), _ptr(T), T.numel(), _ptr(U), _ptr(C),
+                             _stream_ptr(stream)))
+
+
+def windows_balanced(cost, h: int, overlap: float = 0.75):
+    """Run-time balanced windows for a per-bin cost profile (host computation)."""
+    c = np.ascontiguousarray(cost, np.float64)
+    a = np.zeros(2 * h, np.int32)
+    _check(lib().rewl_windows_balanced(_ptr(c), len(c) - 1, int(h), float(overlap), _ptr(a)))
+    return a[:h].copy(), a[h:].copy()
+
+
+MLP_NPARAM = 4481
+
+
+def _mcheck(rc):
+    if rc != 0:
+        raise REWLError(f"rewl error {rc}: {lib().rewl_mlp_last_error().decode()}")
+
+
+def mlp_forward(P, X, Y, stream=None):
+    _mcheck(lib().rewl_mlp_forward(_ptr(P), _ptr(X), _ptr(Y), X.shape[0], _stream_ptr(stream)))
+
+
+def mlp_workspace_floats(n: int) -> int:
+    return int(lib().rewl_mlp_workspace_floats(int(n)))
+
+
+def mlp_grad(P, X, T, grad, loss, work, stream=None):
+    _mcheck(lib().rewl_mlp_grad(_ptr(P), _ptr(X), _ptr(T), X.shape[0], _ptr(grad), _ptr(loss),
+                                _ptr(work), _stream_ptr(stream)))
+
+
+def mlp_adam(P, grad, m, v, t, lr, stream=None):
+    _mcheck(lib().rewl_mlp_adam(_ptr(P), _ptr(grad), _ptr(m), _ptr(v), int(t), float(lr),
+                                _stream_ptr(stream)))
+
+
+def mlp_train(P, X, T, steps, lr, t0, m, v, grad, work, loss, stream=None):
+    _mcheck(lib().rewl_mlp_train(_ptr(P), _ptr(X), _ptr(T), X.shape[0], int(steps), float(lr),
+                                 int(t0), _ptr(m), _ptr(v), _ptr(grad), _ptr(work), _ptr(loss),
+                                 _stream_ptr(stream)))
+
+
+def mlp_init(P, seed, stream=None):
+    _mcheck(lib().rewl_mlp_init(_ptr(P), int(seed) & (2 ** 64 - 1), _stream_ptr(stream)))
+
+
+def mlp_samples(lng, model, L, X, T, count, stream=None):
+    _mcheck(lib().rewl_mlp_samples(_ptr(lng), int(model), int(L), _ptr(X), _ptr(T), _ptr(count),
+                                   _stream_ptr(stream)))
+
+
+def mlp_predict(P, model, L, out, stream=None):
+    _mcheck(lib().rewl_mlp_predict(_ptr(P), int(model), int(L), _ptr(out), _stream_ptr(stream)))
 
 
 REPLAY_STATIC_MAX_N = 16384

@@ -35,3 +35,20 @@ def random_lng(rng, n, W, scale=3.0, offset=0.0):
 
 def random_H(rng, n, W, hi=1000):
     return rng.integers(0, hi, size=(n, W)).astype(np.uint32)
+
+
+def mlp_params(seed, nparam=4481, scale=0.3):
+    """Random MLP parameter vector (float32-representable) for the gradient tests."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, scale, nparam).astype(np.float32).astype(np.float64)
+
+
+def mlp_data(seed, n):
+    """Features (e in [-2, 0], q in {2, 10}, 1/L in [1/32, 1/8]) and smooth targets."""
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(-2.0, 0.0, n)
+    q = rng.choice([2.0, 10.0], n)
+    il = 1.0 / rng.choice([8.0, 12.0, 16.0, 24.0, 32.0], n)
+    X = np.stack([e, q, il], axis=1).astype(np.float32)
+    T = (np.log(q) * (1 + e / 2.0) ** 0.5 * (1 - il)).astype(np.float32)
+    return X, T

@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FIELDS = ["spins", "k", "lng", "H", "step", "acc", "flat", "lnf", "iter", "finished", "mask",
-          "swap_att", "swap_acc", "pstep", "prep_restarts", "round"]
+          "swap_att", "swap_acc", "pstep", "prep_restarts", "round", "first_iter_round", "mode", "frag"]
 
 
 @pytest.fixture(scope="module")

@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FIELDS = ["spins", "k", "lng", "H", "step", "acc", "flat", "lnf", "iter", "finished", "mask",
-          "swap_att", "swap_acc", "pstep", "prep_restarts", "round"]
+          "swap_att", "swap_acc", "pstep", "prep_restarts", "round", "first_iter_round", "mode", "frag"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -34,7 +34,7 @@ def _pair(model, L, h, m, lnf_final=1e-6, flat=0.8, seed=1, interval=1000, **kw)
     import paper_1402_2328_gb300.rewl as R
     g = R.REWL(model, L, h, 0.75, m, lnf_final, flat, seed=seed, interval=interval, **kw)
     o = O.REWL(model, L, h, 0.75, m, lnf_final, flat, seed=seed, interval=interval,
-               lnf_init=kw.get("lnf_init", 1.0))
+               lnf_init=kw.get("lnf_init", 1.0), schedule=kw.get("schedule", 0))
     return g, o
 
 
@@ -213,6 +213,58 @@ def test_full_size_rounds_bit_exact(model, L, h, m, rounds):
     o.run(rounds)
     _same(g.state(), o.state())
     g.close()
+
+
+@pytest.mark.parametrize("model,L,h,m,interval", [(0, 6, 2, 2, 400), (3, 5, 2, 2, 300)])
+def test_one_over_t_schedule_to_completion_bit_exact(model, L, h, m, interval):
+    """The 1/t schedule: ln f = visited bins / moves after the switch, averaged every check."""
+    g, o = _pair(model, L, h, m, lnf_final=1e-5, seed=31 + L, interval=interval, schedule=1)
+    assert g.run() == "done"
+    o.init()
+    o.run(10 ** 7)
+    st = g.state()
+    _same(st, o.state())
+    assert np.all(st["mode"] == 1) and np.all(st["first_iter_round"] > 0)
+    g.close()
+
+
+def test_jackknife_gpu_equals_oracle():
+    g, o = _pair(0, 6, 3, 4, lnf_final=1e-5, seed=41, interval=500)
+    assert g.run() == "done"
+    o.init()
+    o.run(10 ** 7)
+    _same(g.state(), o.state(), FIELDS + ["frag"])
+    eg, eo = g.jackknife(0), o.jackknife(0)
+    fin = np.isfinite(eo)
+    assert np.array_equal(np.isfinite(eg), fin) and fin.sum() > 10
+    assert np.max(np.abs(eg[fin] - eo[fin])) < 1e-9
+    assert np.all(eg[fin] >= 0) and np.max(eg[fin]) < 1.0
+    g.close()
+
+
+def test_balanced_windows_pipeline():
+    """Pre-run with equal windows until every first iteration ended, then balanced windows."""
+    import paper_1402_2328_gb300.rewl as R
+    pre = R.REWL(0, 16, 8, 0.75, 2, 1e-3, 0.8, seed=5, interval=2000)
+    pre.init()
+    for _ in range(200):
+        pre.run(max_rounds=5)
+        if np.all(pre.get_state("first_iter_round") > 0):
+            break
+    t1 = pre.get_state("first_iter_round")
+    assert np.all(t1 > 0)
+    lo, hi = pre.balanced_windows(8, 0.75)
+    assert lo[0] == 0 and hi[-1] == 256 and np.all(lo[1:] <= hi[:-1])
+    r = R.REWL(0, 16, 8, 0.75, 2, 1e-4, 0.8, seed=6, interval=2000)
+    r.set_windows(lo, hi)
+    assert r.run() == "done"
+    out, joins = r.stitch(0)
+    ex = X.normalise_lng(np.array(X.exact_lng(0, 16)), 256 * math.log(2))
+    fin = np.isfinite(ex)
+    assert np.array_equal(np.isfinite(out), fin)
+    assert np.max(np.abs(out[fin] - ex[fin])) < 1.0
+    pre.close()
+    r.close()
 
 
 def test_stitch_gpu_equals_oracle_partial_run():
