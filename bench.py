@@ -37,6 +37,8 @@ WORKLOADS = {
                               lnf_final=1e-8, flatness=0.8, interval=10_000, config_id=2),
     "potts10_L40_h64_m16": dict(model=10, L=40, windows=64, walkers=16, overlap=0.75,
                                 lnf_final=1e-8, flatness=0.8, interval=10_000, config_id=3),
+    "potts10_L80_h64_m16": dict(model=10, L=80, windows=64, walkers=16, overlap=0.75,
+                                lnf_final=1e-8, flatness=0.8, interval=10_000, config_id=5),
     "ising_L8_h4_m1": dict(model=0, L=8, windows=4, walkers=1, overlap=0.75,
                            lnf_final=1e-6, flatness=0.8, interval=10_000, config_id=1),
     # 24 uneven instances in one launch per round: (model, L) cycles Ising 16/32/64 and
@@ -147,6 +149,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ----------------------------------------------------------------------------- ranks
+def max_over_ranks(values, device=None):
+    """Element-wise max of per-rank timings (all_reduce MAX); identity on one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(per_rank_units, world, rank_ms):
+    """Weak scaling: units of all ranks divided by the slowest rank's time."""
+    return per_rank_units * world / (rank_ms / 1e3)
+
+
 # ----------------------------------------------------------------------------- main arms
 def _roofline(per_launch_attempts, move_ms, move_launches, sms, step_ms):
     peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
@@ -223,14 +243,10 @@ def run_gpu_batch(args, wl, rank, world):
         torch.cuda.synchronize()
         solo_ms += a.elapsed_time(z)
         g.close()
-    t_max = step_ms
-    if world > 1:
-        t = torch.tensor([step_ms, e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max, e2e_s = float(t[0]), float(t[1])
+    t_max, e2e_s = max_over_ranks([step_ms, e2e_s], device="cuda")
     attempts = per_round * args.steps * world
     return {
-        "metric": METRIC, "value": attempts / (t_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": whole_job_rate(per_round * args.steps, world, t_max), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64",
         "data": "synthetic",
@@ -309,6 +325,104 @@ def run_full(args, wl):
     return out
 
 
+def run_warm(args):
+    """Learned warm start: plain REWL on Ising and q=10 Potts, L = 8..32 (one batched launch
+    per round) -> joined ln g -> MLP trained on the GPU -> predicted ln g of the target lattice;
+    then the target run cold (ln f0 = 1) and warm (predicted ln g, small ln f0), timed."""
+    import numpy as np
+    import torch
+    import paper_1402_2328_gb300.rewl as R
+    from paper_1402_2328_gb300 import warm as WM
+
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    descs = []
+    for i, (model, L) in enumerate(WM.TRAIN_LATTICES):
+        B = L * L if model == 0 else 2 * L * L
+        h = max(2, min(16, B // 128))
+        descs.append(dict(model=model, L=L, windows=h, walkers=4, lnf_final=args.train_lnf_final,
+                          seed=seed_for(5, 500 + i), instance=i))
+    b = R.REWLBatch(descs, interval=10_000)
+    st = b.run(max_seconds=args.max_seconds)
+    t_train_runs = time.perf_counter() - t0
+    runs, train_stats = [], []
+    # learned window boundaries: the first-iteration cost profile of the largest training
+    # lattice of the target model, carried to the target lattice by energy per site
+    big = max((i for i, d in enumerate(descs) if d["model"] == args.warm_model),
+              key=lambda i: descs[i]["L"])
+    lw_lo, lw_hi = b.instance(big).balanced_windows_for(args.warm_L, args.warm_windows, 0.75)
+    for i, d in enumerate(descs):
+        inst = b.instance(i)
+        s_i = inst.stats()
+        if s_i["windows_finished"] == inst.h:
+            lng, _ = inst.stitch(0)
+            runs.append((d["model"], d["L"], lng))
+        train_stats.append(dict(model=d["model"], L=d["L"], windows=d["windows"],
+                                rounds=s_i["rounds"], finished=s_i["windows_finished"] == inst.h))
+    b.close()
+    X, T = WM.training_set(runs)
+    t1 = time.perf_counter()
+    P, hist = WM.train(X, T, steps=args.train_steps, lr=3e-3, seed=seed_for(5, 999))
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t1
+    lng_pred = WM.predict_lng(P, args.warm_model, args.warm_L)
+
+    def target(seed, kind):
+        if kind.startswith("warm"):
+            r = WM.warm_handle(args.warm_model, args.warm_L, args.warm_windows, args.warm_walkers,
+                               args.warm_lnf_final, seed, lng_pred, lnf_init=args.warm_lnf_init)
+        else:
+            r = R.REWL(args.warm_model, args.warm_L, args.warm_windows, 0.75, args.warm_walkers,
+                       args.warm_lnf_final, 0.8, seed=seed, interval=10_000)
+        if kind in ("warm", "cold_lw"):
+            r.set_windows(lw_lo, lw_hi)
+        ts = time.perf_counter()
+        status = r.run(max_seconds=args.max_seconds)
+        dt = time.perf_counter() - ts
+        s_r = r.stats()
+        out = dict(status=status, seconds=dt, rounds=s_r["rounds"], attempts=s_r["attempts"],
+                   windows_finished=s_r["windows_finished"], max_lnf=s_r["max_lnf"])
+        lng = r.stitch(0)[0] if status == "done" else None
+        r.close()
+        return out, lng
+
+    results, lngs = {}, {}
+    for kind in args.warm_variants.split(","):
+        results[kind], lngs[kind] = target(seed_for(5, 1), kind)
+    cold = results.get("cold")
+    warm = results.get("warm")
+    lng_cold, lng_warm = lngs.get("cold"), lngs.get("warm")
+
+    def maxdiff(a, b_):
+        if a is None or b_ is None:
+            return None
+        fin = np.isfinite(a) & np.isfinite(b_)
+        return float(np.max(np.abs(a[fin] - b_[fin])))
+
+    N = args.warm_L ** 2
+    q = 2 if args.warm_model == 0 else args.warm_model
+    pred = np.array(lng_pred, np.float64)
+    mx = pred.max()
+    pred_n = pred - (mx + math.log(np.exp(pred - mx).sum()) - N * math.log(q))
+    if lng_cold is not None:
+        pred_n = np.where(np.isfinite(lng_cold), pred_n, -np.inf)
+    np.save(os.path.join(ROOT, "gpurun_out", "warm_lng_pred.npy"), pred) if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else None
+    return {"warm_start": {
+        "target": dict(model=args.warm_model, L=args.warm_L, windows=args.warm_windows,
+                       walkers_per_window=args.warm_walkers, lnf_final=args.warm_lnf_final,
+                       lnf_init_warm=args.warm_lnf_init),
+        "training_runs": train_stats, "training_status": st,
+        "training_runs_seconds": t_train_runs, "training_samples": int(X.shape[0]),
+        "fit_seconds": t_fit, "fit_loss": hist[-1][1],
+        "runs": results, "learned_windows": {"lo": lw_lo.tolist(), "hi": lw_hi.tolist()},
+        "speedup_time": (cold["seconds"] / warm["seconds"])
+        if cold and warm and warm["status"] == "done" and cold["status"] == "done" else None,
+        "max_abs_dlng_warm_vs_cold": maxdiff(lng_warm, lng_cold),
+        "max_abs_dlng_prediction_vs_cold": maxdiff(pred_n, lng_cold),
+    }}
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     import paper_1402_2328_gb300.rewl as R
@@ -358,13 +472,9 @@ def run_gpu(args, wl, rank, world):
         r.run(max_rounds=1)
         _ = r.get_state("lng_mean")
     e2e_s = time.perf_counter() - t0
-    t_max = step_ms
-    if world > 1:
-        t = torch.tensor([step_ms, e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max, e2e_s = float(t[0]), float(t[1])
+    t_max, e2e_s = max_over_ranks([step_ms, e2e_s], device="cuda")
     attempts = per_round * args.steps * world
-    value = attempts / (t_max / 1e3)
+    value = whole_job_rate(per_round * args.steps, world, t_max)
     # roofline of the move kernel (ALU/issue bound)
     peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -414,6 +524,19 @@ def main():
     ap.add_argument("--full-run", action="store_true",
                     help="run the workload to ln f < ln f_final and report the time to solution")
     ap.add_argument("--max-seconds", type=float, default=1800.0, help="cap of --full-run")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="learned warm start experiment: train on small lattices, compare "
+                         "warm vs cold on the target lattice")
+    ap.add_argument("--warm-model", type=int, default=10)
+    ap.add_argument("--warm-L", type=int, default=80)
+    ap.add_argument("--warm-windows", type=int, default=64)
+    ap.add_argument("--warm-walkers", type=int, default=16)
+    ap.add_argument("--warm-lnf-final", type=float, default=1e-8)
+    ap.add_argument("--warm-lnf-init", type=float, default=1e-3)
+    ap.add_argument("--train-lnf-final", type=float, default=1e-6)
+    ap.add_argument("--train-steps", type=int, default=6000)
+    ap.add_argument("--warm-variants", default="cold,warm",
+                    help="comma list of cold | warm | cold_lw | warm_eq (lw: learned windows)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -424,6 +547,9 @@ def main():
 
     if args.full_run:
         print(json.dumps({"full_run": run_full(args, wl)}))
+        return
+    if args.warm_start:
+        print(json.dumps(run_warm(args)))
         return
 
     if args.impl == "reference":

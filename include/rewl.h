@@ -113,6 +113,12 @@ int rewl_windows_balanced(const double *cost, int B, int h, double overlap, int 
  * rewl_windows_balanced with h windows.  Use the result with rewl_set_windows on a new handle.
  */
 int rewl_balanced_from_prerun(rewl_t pre, int h, double overlap, int *lo_hi);
+/*
+ * rewl_balanced_scaled -- the same cost profile carried over to the same model on an L x L
+ * lattice (bins matched by energy per site, e = E/N), then rewl_windows_balanced with h windows
+ * over that lattice's bins: window boundaries for a large lattice learned from a smaller one.
+ */
+int rewl_balanced_scaled(rewl_t pre, int L, int h, double overlap, int *lo_hi);
 
 /* rewl_set_stream -- cudaStream_t (as void*) for all later work of this handle. */
 int rewl_set_stream(rewl_t r, void *stream);

@@ -605,16 +605,17 @@ int rewl_windows_balanced(const double *cost, int B, int h, double overlap, int 
     return REWL_OK;
 }
 
-int rewl_balanced_from_prerun(rewl_t pre, int h, double overlap, int *lo_hi)
+// per-bin first-iteration cost density of a run: mean over the windows covering the bin of
+// (first-iteration rounds) / (window width)
+static int prerun_cost(rewl_t pre, std::vector<double> &c)
 {
-    if (!pre || !lo_hi || h < 1) return REWL_ERR_INVALID_ARG;
     std::vector<long long> t1((size_t)pre->h);
     int rc = rewl_get_state(pre, "first_iter_round", t1.data(), t1.size() * 8);
     if (rc != REWL_OK) return rc;
     for (long long v : t1)
         if (v <= 0) return pre->fail(REWL_ERR_STATE, "pre-run: a window has not finished its first iteration");
-    // per-bin cost density: mean over the windows covering the bin of t_w / width_w
-    std::vector<double> c((size_t)pre->B + 1, 0.0), n((size_t)pre->B + 1, 0.0);
+    std::vector<double> n((size_t)pre->B + 1, 0.0);
+    c.assign((size_t)pre->B + 1, 0.0);
     for (int w = 0; w < pre->h; ++w) {
         const double d = (double)t1[w] / (double)(pre->hi[w] - pre->lo[w] + 1);
         for (int b = pre->lo[w]; b <= pre->hi[w]; ++b) {
@@ -623,7 +624,35 @@ int rewl_balanced_from_prerun(rewl_t pre, int h, double overlap, int *lo_hi)
         }
     }
     for (int b = 0; b <= pre->B; ++b) c[b] = n[b] > 0 ? c[b] / n[b] : 0.0;
+    return REWL_OK;
+}
+
+int rewl_balanced_from_prerun(rewl_t pre, int h, double overlap, int *lo_hi)
+{
+    if (!pre || !lo_hi || h < 1) return REWL_ERR_INVALID_ARG;
+    std::vector<double> c;
+    int rc = prerun_cost(pre, c);
+    if (rc != REWL_OK) return rc;
     rc = rewl_windows_balanced(c.data(), pre->B, h, overlap, lo_hi);
+    if (rc != REWL_OK) return pre->fail(rc, g_err);
+    return REWL_OK;
+}
+
+int rewl_balanced_scaled(rewl_t pre, int L, int h, double overlap, int *lo_hi)
+{
+    if (!pre || !lo_hi || h < 1 || L < 2) return REWL_ERR_INVALID_ARG;
+    std::vector<double> c;
+    int rc = prerun_cost(pre, c);
+    if (rc != REWL_OK) return rc;
+    // the same model on an L x L lattice: bins map through e = E/N (energy per site)
+    const int N = L * L, B = pre->model == 0 ? N : 2 * N;
+    std::vector<double> cs((size_t)B + 1);
+    for (int b = 0; b <= B; ++b) {
+        const double frac = (double)b / (double)B; // e = -2 + (2 or 1) * b/N, linear in b/B
+        const int bp = (int)std::lround(frac * (double)pre->B);
+        cs[b] = c[(size_t)std::min(std::max(bp, 0), pre->B)];
+    }
+    rc = rewl_windows_balanced(cs.data(), B, h, overlap, lo_hi);
     if (rc != REWL_OK) return pre->fail(rc, g_err);
     return REWL_OK;
 }

@@ -72,6 +72,7 @@ def lib():
             "rewl_thermo": ([P, I, I, P, I, P, P, P], I),
             "rewl_jackknife": ([P, P, I, I], I),
             "rewl_balanced_from_prerun": ([P, I, D, P], I),
+            "rewl_balanced_scaled": ([P, I, I, D, P], I),
             "rewl_mlp_forward": ([P, P, P, I, P], I),
             "rewl_mlp_workspace_floats": ([I], I),
             "rewl_mlp_grad": ([P, P, P, I, P, P, P, P], I),
@@ -223,6 +224,13 @@ class REWL:
         """Windows balanced by this (pre-)run's first-iteration times (Fig. 1b)."""
         a = np.zeros(2 * h, np.int32)
         _check(self._lib.rewl_balanced_from_prerun(self._h, int(h), float(overlap), _ptr(a)),
+               self._h)
+        return a[:h].copy(), a[h:].copy()
+
+    def balanced_windows_for(self, L: int, h: int, overlap: float = 0.75):
+        """This run's first-iteration cost profile carried to an L x L lattice (by E/N)."""
+        a = np.zeros(2 * h, np.int32)
+        _check(self._lib.rewl_balanced_scaled(self._h, int(L), int(h), float(overlap), _ptr(a)),
                self._h)
         return a[:h].copy(), a[h:].copy()
 
