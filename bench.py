@@ -321,6 +321,17 @@ def run_full(args, wl):
             ex = ex - (mx + math.log(np.exp(ex[fin] - mx).sum()) - r.N * math.log(2))
             out["max_abs_dlng_vs_exact"] = float(np.max(np.abs(lng[fin] - ex[fin])))
             out["rms_dlng_vs_exact"] = float(np.sqrt(np.mean((lng[fin] - ex[fin]) ** 2)))
+        if r.m >= 2:
+            # jackknife error bars over the m walkers' fragments (Sec. 3); the paper finds the
+            # deviation from the exact result of the order of the statistical error
+            err = r.jackknife(0)
+            ok = np.isfinite(err) & np.isfinite(lng)
+            out["jackknife_max"] = float(err[ok].max())
+            out["jackknife_rms"] = float(np.sqrt(np.mean(err[ok] ** 2)))
+            if ex is not None:
+                okx = ok & np.isfinite(ex)
+                out["rms_dlng_over_jackknife_rms"] = float(
+                    np.sqrt(np.mean((lng[okx] - ex[okx]) ** 2)) / np.sqrt(np.mean(err[okx] ** 2)))
     r.close()
     return out
 
@@ -421,6 +432,71 @@ def run_warm(args):
         "max_abs_dlng_warm_vs_cold": maxdiff(lng_warm, lng_cold),
         "max_abs_dlng_prediction_vs_cold": maxdiff(pred_n, lng_cold),
     }}
+
+
+def run_speedup(args):
+    """Eq. (5): s_o(h, m) = N_single / N_o(h, m), N = MC moves of the slowest walker until the
+    first WL iteration is complete ((rounds until the last window's first halving) x interval).
+    Equal windows (Fig. 1a) for h in --speedup-h, then run-time balanced windows (Fig. 1b) built
+    from each equal-window run's first-iteration times, run with new seeds.  Every (h, seed)
+    instance of a phase advances in one batched launch per round; ln f_final = 0.75 stops each
+    window at its first halving."""
+    import numpy as np
+    import torch
+    import paper_1402_2328_gb300.rewl as R
+
+    torch.cuda.set_device(0)
+    model, L, m = args.speedup_model, args.speedup_L, args.speedup_walkers
+    hs = [int(x) for x in args.speedup_h.split(",")]
+    S, interval = args.speedup_seeds, args.speedup_interval
+
+    def phase(layouts, seed_base):
+        descs, keys = [], []
+        for (h, s) in sorted(layouts):
+            descs.append(dict(model=model, L=L, windows=h, walkers=m, lnf_final=0.75,
+                              seed=seed_for(6, seed_base + 100 * h + s), instance=len(descs)))
+            keys.append((h, s))
+        b = R.REWLBatch(descs, interval=interval)
+        for i, k in enumerate(keys):
+            if layouts[k] is not None:
+                b.instance(i).set_windows(*layouts[k])
+        b.init()
+        t0 = time.perf_counter()
+        status = b.run(max_seconds=args.max_seconds)
+        sec = time.perf_counter() - t0
+        res = {}
+        for i, k in enumerate(keys):
+            inst = b.instance(i)
+            t1 = inst.get_state("first_iter_round").astype(np.int64)
+            res[k] = dict(t1=t1, lohi=inst.balanced_windows(k[0], 0.75) if k[0] > 1 else None,
+                          width=(inst.get_state("hi") - inst.get_state("lo") + 1))
+        b.close()
+        return res, status, sec
+
+    eq, st_eq, sec_eq = phase({(h, s): None for h in hs for s in range(S)}, 0)
+    bal_layouts = {(h, s): eq[(h, s)]["lohi"] for h in hs if h > 1 for s in range(S)}
+    bal, st_bal, sec_bal = phase(bal_layouts, 50_000)
+
+    def summary(res, h):
+        n = [res[(h, s)]["t1"].max() * interval for s in range(S) if res[(h, s)]["t1"].min() > 0]
+        spread = [res[(h, s)]["t1"].max() / res[(h, s)]["t1"].min() for s in range(S)
+                  if res[(h, s)]["t1"].min() > 0]
+        return (float(np.mean(n)) if n else None, float(np.mean(spread)) if spread else None,
+                len(n))
+
+    n_single, _, _ = summary(eq, 1) if 1 in hs else (None, None, 0)
+    rows = []
+    for h in hs:
+        ne, sp_e, ok_e = summary(eq, h)
+        nb, sp_b, ok_b = summary(bal, h) if h > 1 else (ne, sp_e, ok_e)
+        rows.append({"h": h, "m": m,
+                     "N_equal": ne, "s_equal": n_single / ne if n_single and ne else None,
+                     "t1_spread_equal": sp_e,
+                     "N_balanced": nb, "s_balanced": n_single / nb if n_single and nb else None,
+                     "t1_spread_balanced": sp_b, "seeds_done": [ok_e, ok_b]})
+    return {"speedup": {"model": model, "L": L, "overlap": 0.75, "walkers_per_window": m,
+                        "interval": interval, "seeds": S, "status": [st_eq, st_bal],
+                        "seconds": [sec_eq, sec_bal], "rows": rows}}
 
 
 def run_gpu(args, wl, rank, world):
@@ -535,6 +611,14 @@ def main():
     ap.add_argument("--warm-lnf-init", type=float, default=1e-3)
     ap.add_argument("--train-lnf-final", type=float, default=1e-6)
     ap.add_argument("--train-steps", type=int, default=6000)
+    ap.add_argument("--speedup", action="store_true",
+                    help="speed-up s_o(h, m) of Eq. (5) with equal and run-time balanced windows")
+    ap.add_argument("--speedup-model", type=int, default=0)
+    ap.add_argument("--speedup-L", type=int, default=32)
+    ap.add_argument("--speedup-walkers", type=int, default=1)
+    ap.add_argument("--speedup-h", default="1,2,4,8,16,32")
+    ap.add_argument("--speedup-seeds", type=int, default=8)
+    ap.add_argument("--speedup-interval", type=int, default=10_000)
     ap.add_argument("--warm-variants", default="cold,warm",
                     help="comma list of cold | warm | cold_lw | warm_eq (lw: learned windows)")
     args = ap.parse_args()
@@ -550,6 +634,9 @@ def main():
         return
     if args.warm_start:
         print(json.dumps(run_warm(args)))
+        return
+    if args.speedup:
+        print(json.dumps(run_speedup(args)))
         return
 
     if args.impl == "reference":

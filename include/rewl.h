@@ -283,7 +283,9 @@ int rewl_batch_run(rewl_batch_t b, double max_seconds, long long max_rounds, int
  */
 int rewl_batch_autotune(rewl_batch_t b, int rounds, int *best, double *ms);
 /* Instance i as a handle for the query calls (get_state, get_lng, stitch, stats,
- * checkpoint); owned by the batch: do not destroy it or run it on its own. */
+ * checkpoint); owned by the batch: do not destroy it or run it on its own.  Before
+ * rewl_batch_init, rewl_set_windows on it replaces the instance's window layout (e.g. run-time
+ * balanced windows, Fig. 1b). */
 int rewl_batch_instance(rewl_batch_t b, int i, rewl_t *out);
 /* out (4 ints): instances, total walkers, CTAs of the move launch, warps per CTA. */
 int rewl_batch_info(rewl_batch_t b, int *out);

@@ -52,6 +52,10 @@ def lib():
                                      C.c_double, C.c_uint64, C.c_uint32, C.c_longlong,
                                      C.c_longlong, C.c_double]
         L.or_rewl_create.restype = P
+        L.or_rewl_create_windows.argtypes = [C.c_int, C.c_int, C.c_int, P, P, C.c_double, C.c_int,
+                                             C.c_double, C.c_double, C.c_uint64, C.c_uint32,
+                                             C.c_longlong, C.c_longlong, C.c_double]
+        L.or_rewl_create_windows.restype = P
         L.or_rewl_destroy.argtypes = [P]
         L.or_rewl_set_lng.argtypes = [P, P]
         L.or_rewl_init.argtypes = [P]
@@ -130,11 +134,21 @@ class REWL:
     def __init__(self, model: int, L: int, windows: int, overlap: float, walkers: int,
                  lnf_final: float, flatness: float, seed: int, instance: int = 0,
                  interval: int = 10_000, prep_budget: int = 100, lnf_init: float = 1.0,
-                 lng_init=None, schedule: int = 0):
+                 lng_init=None, schedule: int = 0, lo_hi=None):
+        """lo_hi: optional (lo, hi) window layout; `windows` must then equal len(lo)."""
         self._lib = lib()
-        self._h = self._lib.or_rewl_create(model, L, windows, overlap, walkers, lnf_final,
-                                           flatness, seed, instance, interval, prep_budget,
-                                           lnf_init)
+        if lo_hi is None:
+            self._h = self._lib.or_rewl_create(model, L, windows, overlap, walkers, lnf_final,
+                                               flatness, seed, instance, interval, prep_budget,
+                                               lnf_init)
+        else:
+            lo = np.ascontiguousarray(lo_hi[0], dtype=np.int32)
+            hi = np.ascontiguousarray(lo_hi[1], dtype=np.int32)
+            if len(lo) != windows or len(hi) != windows:
+                raise ValueError("oracle: lo_hi does not have `windows` entries")
+            self._h = self._lib.or_rewl_create_windows(model, L, windows, _p(lo), _p(hi), overlap,
+                                                       walkers, lnf_final, flatness, seed,
+                                                       instance, interval, prep_budget, lnf_init)
         if not self._h:
             raise ValueError("oracle: invalid REWL parameters")
         d = np.zeros(5, dtype=np.int32)

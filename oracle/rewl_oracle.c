@@ -309,9 +309,12 @@ void or_rewl_destroy(or_rewl *r)
     free(r);
 }
 
-or_rewl *or_rewl_create(int model, int L, int h, double overlap, int m, double lnf_final,
-                        double flatness, uint64_t seed, uint32_t inst, long long interval,
-                        long long prep_budget, double lnf_init)
+/* Windows given by the caller (lo[0] = 0, hi[h-1] = B, each next window starting inside the
+ * previous one); NULL lo/hi: the equal-size layout of Fig. 1a with overlap `overlap`. */
+or_rewl *or_rewl_create_windows(int model, int L, int h, const int *lo_in, const int *hi_in,
+                                double overlap, int m, double lnf_final, double flatness,
+                                uint64_t seed, uint32_t inst, long long interval,
+                                long long prep_budget, double lnf_init)
 {
     if (L < 2 || h < 1 || m < 1 || (model != 0 && model < 2) || interval < 1) return NULL;
     or_rewl *r = (or_rewl *)zalloc(sizeof(or_rewl));
@@ -333,7 +336,20 @@ or_rewl *or_rewl_create(int model, int L, int h, double overlap, int m, double l
     r->prep_budget = prep_budget;
     r->lo = (int *)zalloc(sizeof(int) * h);
     r->hi = (int *)zalloc(sizeof(int) * h);
-    if (or_windows(r->B, h, overlap, r->lo, r->hi) != 0) { or_rewl_destroy(r); return NULL; }
+    if (lo_in && hi_in) {
+        for (int w = 0; w < h; w++) {
+            r->lo[w] = lo_in[w];
+            r->hi[w] = hi_in[w];
+        }
+        int bad = r->lo[0] != 0 || r->hi[h - 1] != r->B;
+        for (int w = 0; w < h; w++) bad |= r->hi[w] <= r->lo[w];
+        for (int w = 0; w + 1 < h; w++)
+            bad |= r->lo[w + 1] <= r->lo[w] || r->lo[w + 1] > r->hi[w] || r->hi[w + 1] < r->hi[w];
+        if (bad) { or_rewl_destroy(r); return NULL; }
+    } else if (or_windows(r->B, h, overlap, r->lo, r->hi) != 0) {
+        or_rewl_destroy(r);
+        return NULL;
+    }
     int W = 0;
     for (int w = 0; w < h; w++)
         if (r->hi[w] - r->lo[w] + 1 > W) W = r->hi[w] - r->lo[w] + 1;
@@ -362,6 +378,14 @@ or_rewl *or_rewl_create(int model, int L, int h, double overlap, int m, double l
         r->finished[w] = lnf_init < lnf_final;
     }
     return r;
+}
+
+or_rewl *or_rewl_create(int model, int L, int h, double overlap, int m, double lnf_final,
+                        double flatness, uint64_t seed, uint32_t inst, long long interval,
+                        long long prep_budget, double lnf_init)
+{
+    return or_rewl_create_windows(model, L, h, NULL, NULL, overlap, m, lnf_final, flatness, seed,
+                                  inst, interval, prep_budget, lnf_init);
 }
 
 /* Optional warm start: ln g over all B+1 bins copied into every walker. */

@@ -173,8 +173,6 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
     // interval-constant part of the float32 screening margin (ln units)
     const float Mbase = (float)(c.eps_l + 2.0 * shadow_error(mx, T, lnf, frozen) * 0x1p-32) + 0x1p-21f;
     const float lnf_f = frozen ? 0.0f : (float)lnf;
-    constexpr int REACH = ISING ? 13 : 11; // cache holds k0-16..k0+15; |dk| <= 2 (Ising), 4 (Potts)
-    const int span = hi - lo;
     __syncwarp();
 
     const unsigned long long st0 = s.step[slot];

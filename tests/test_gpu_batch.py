@@ -96,6 +96,27 @@ def test_batch_to_completion_equals_solo(R):
     b.close()
 
 
+def test_batch_instance_with_caller_windows(R):
+    """Windows replaced on a batch instance before init: the instance equals the oracle."""
+    descs = [dict(model=0, L=16, windows=5, walkers=2, lnf_final=1e-4, seed=31, instance=0),
+             dict(model=10, L=8, windows=4, walkers=2, lnf_final=1e-4, seed=32, instance=1)]
+    cost = np.ones(257)
+    cost[200:] = 6.0
+    lo, hi = R.windows_balanced(cost, 5, 0.75)
+    b = R.REWLBatch(descs, interval=600)
+    b.instance(0).set_windows(lo, hi)
+    b.init()
+    b.run(max_rounds=25)
+    for i, d in enumerate(descs):
+        o = O.REWL(d["model"], d["L"], d["windows"], 0.75, d["walkers"], d["lnf_final"], 0.8,
+                   seed=d["seed"], instance=d["instance"], interval=600,
+                   lo_hi=(lo, hi) if i == 0 else None)
+        assert o.init() == 0
+        o.run(25)
+        _same(b.instance(i).state(), o.state())
+    b.close()
+
+
 def test_config4_batch_autotuned_equals_solo(R):
     descs = config4_descs()
     b = R.REWLBatch(descs, interval=10_000)

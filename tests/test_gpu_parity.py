@@ -267,6 +267,25 @@ def test_balanced_windows_pipeline():
     r.close()
 
 
+def test_caller_windows_bit_exact():
+    """Uneven caller windows (balanced layouts): GPU rounds equal the oracle's bit for bit."""
+    import paper_1402_2328_gb300.rewl as R
+    cost = np.ones(257)
+    cost[:60] = 8.0
+    for model, L, h, m, lohi in [(0, 16, 6, 2, R.windows_balanced(cost, 6, 0.75)),
+                                 (3, 8, 4, 3, R.windows_balanced(np.linspace(4, 1, 129), 4, 0.75))]:
+        lo, hi = lohi
+        g = R.REWL(model, L, h, 0.75, m, 1e-4, 0.8, seed=9 + model, interval=700)
+        g.set_windows(lo, hi)
+        o = O.REWL(model, L, h, 0.75, m, 1e-4, 0.8, seed=9 + model, interval=700, lo_hi=(lo, hi))
+        g.init()
+        assert o.init() == 0
+        g.run(max_rounds=30)
+        o.run(30)
+        _same(g.state(), o.state())
+        g.close()
+
+
 def test_stitch_gpu_equals_oracle_partial_run():
     g, o = _pair(3, 6, 4, 2, seed=5, interval=800)
     g.init()

@@ -69,6 +69,33 @@ def test_converges_to_exact(model, L, q, h, m, tol):
     assert np.abs(bias).max() < tol / 2, bias
 
 
+def test_caller_windows():
+    """Windows given by the caller: the equal layout passed explicitly reproduces the default
+    run bit for bit, and an uneven layout (Fig. 1b style) still converges to the exact g(E)."""
+    a = O.REWL(0, 6, 3, 0.75, 2, 1e-3, 0.8, seed=77, interval=300)
+    b = O.REWL(0, 6, 3, 0.75, 2, 1e-3, 0.8, seed=77, interval=300, lo_hi=O.windows(36, 3, 0.75))
+    for r in (a, b):
+        assert r.init() == 0
+        r.run(25)
+    sa, sb = a.state(), b.state()
+    for f in ("spins", "k", "lng", "H", "lnf", "swap_acc"):
+        assert np.array_equal(np.asarray(sa[f]), np.asarray(sb[f])), f
+    with pytest.raises(ValueError):
+        O.REWL(0, 4, 2, 0.75, 1, 1e-3, 0.8, seed=1, lo_hi=([0, 9], [8, 16]))  # no overlap
+    ex = _exact(0, 4)
+    fin = np.isfinite(ex)
+    errs = []
+    for seed in range(3):
+        r = O.REWL(0, 4, 3, 0.75, 4, 1e-6, 0.8, seed=300 + seed, interval=200,
+                   lo_hi=([0, 3, 6], [6, 10, 16]))
+        assert r.init() == 0
+        r.run(10 ** 7)
+        out, _ = r.stitch(0)
+        assert np.array_equal(np.isfinite(out), fin)
+        errs.append(np.abs(out[fin] - ex[fin]).max())
+    assert max(errs) < 0.12, errs
+
+
 def test_ising_8x8_config1_shape():
     ex = _exact(0, 8)
     fin = np.isfinite(ex)
