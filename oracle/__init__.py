@@ -71,6 +71,14 @@ def lib():
         L.or_rewl_get_extra.argtypes = [P, P, P, P]
         L.or_stitch.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, C.c_double, C.c_int,
                                 C.c_int, C.c_double, P, P]
+        L.or_ln.argtypes = [C.c_double]
+        L.or_ln.restype = C.c_double
+        L.or_rewl_measure_em.argtypes = [P, C.c_int]
+        L.or_rewl_set_production.argtypes = [P, C.c_int]
+        L.or_rewl_get_hem.argtypes = [P, P]
+        L.or_frag_em.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P]
+        L.or_join_em.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, C.c_double,
+                                 C.c_double, C.c_double, P, P]
         _lib = L
     return _lib
 
@@ -237,6 +245,33 @@ class REWL:
         err[fin] = np.sqrt((m - 1) / m * ((th[:, fin] - mean) ** 2).sum(axis=0))
         return err
 
+    def measure_em(self, on: bool = True):
+        """Count every walker's (bin, up spins) after the moves of each round (Ising)."""
+        if self._lib.or_rewl_measure_em(self._h, int(on)) != 0:
+            raise ValueError("oracle: (E, M) measurement needs the Ising model")
+
+    def set_production(self, on: bool = True):
+        """run() keeps going after every window finished (frozen ln g)."""
+        self._lib.or_rewl_set_production(self._h, int(on))
+
+    def hist_em(self) -> np.ndarray:
+        out = np.zeros((self.h, self.W, self.N + 1), np.uint32)
+        if self._lib.or_rewl_get_hem(self._h, _p(out)) != 0:
+            raise ValueError("oracle: (E, M) measurement is off")
+        return out
+
+    def window_means(self) -> np.ndarray:
+        lngw = np.zeros((self.h, self.W), np.float64)
+        for w in range(self.h):
+            mwin = self.window_mean(w)
+            lngw[w, : len(mwin)] = mwin
+        return lngw
+
+    def stitch_em(self):
+        """Joint ln g(E, M) over (B+1) x (N+1) points (Sec. 3, Eqs. 3-4)."""
+        S = frag_em(self.lo, self.hi, self.window_means(), self.state()["mask"], self.hist_em())
+        return join_em(self.lo, self.hi, S, self.B, self.N)
+
     def stitch(self, norm: int = 0):
         """Joined ln g over the B+1 bins (Sec. 3, Eq. 2) from the window means."""
         st = self.state()
@@ -265,4 +300,37 @@ def stitch(model: int, L: int, lo, hi, lngw, valid, norm: int = 0):
                          _p(out), _p(joins))
     if rc != 0:
         raise ValueError("oracle stitch: cannot join windows")
+    return out, joins[: h - 1]
+
+
+def ln(x: float) -> float:
+    """The oracle's deterministic logarithm (exponent split + atanh series), x > 0 normal."""
+    return float(lib().or_ln(float(x)))
+
+
+def frag_em(lo, hi, mean, valid, hem):
+    """Fragments S_w(k, j) = mean ln g_w(k) + ln H_w(k, j) - ln sum_j H_w(k, j) (-inf where
+    absent); mean/valid [h][W], hem [h][W][N+1] -> [h][W][N+1]."""
+    hem = np.ascontiguousarray(hem, np.uint32)
+    h, W, N1 = hem.shape
+    S = np.zeros((h, W, N1), np.float64)
+    lib().or_frag_em(h, W, N1, _p(np.ascontiguousarray(lo, np.int32)),
+                     _p(np.ascontiguousarray(hi, np.int32)),
+                     _p(np.ascontiguousarray(mean, np.float64)),
+                     _p(np.ascontiguousarray(valid, np.uint8)), _p(hem), _p(S))
+    return S
+
+
+def join_em(lo, hi, S, B: int, N: int):
+    """Joint ln g(E, M) from window fragments S [h][W][N+1] (Ising: dE = 4 per bin, dM = 2 per
+    up spin), normalised to sum g = 2^N.  Returns ((B+1) x (N+1) array, joins [h-1][2])."""
+    S = np.ascontiguousarray(S, np.float64)
+    h, W, N1 = S.shape
+    out = np.zeros((B + 1, N1), np.float64)
+    joins = np.zeros((max(h - 1, 1), 2), np.int32)
+    rc = lib().or_join_em(h, W, B, N1, _p(np.ascontiguousarray(lo, np.int32)),
+                          _p(np.ascontiguousarray(hi, np.int32)), _p(S), 4.0, 2.0,
+                          N * np.log(2.0), _p(out), _p(joins))
+    if rc != 0:
+        raise ValueError("oracle join_em: adjacent fragments share no point")
     return out, joins[: h - 1]

@@ -285,6 +285,63 @@ def kaufman_ising(L: int) -> list[int]:
 
 
 @lru_cache(maxsize=None)
+def brute_force_ising_em(L: int) -> np.ndarray:
+    """g[k][j] (int64): configurations with k = n_u / 2 unsatisfied-bond pairs and j spins up
+    (magnetisation M = 2j - N), by enumerating all 2^N configurations (N <= 20)."""
+    N = L * L
+    if N > 20:
+        raise ValueError("brute force (E, M) only for N <= 20")
+    idx = np.arange(1 << N, dtype=np.int64)
+    up = ((idx[:, None] >> np.arange(N)) & 1).astype(np.int8)
+    s = (2 * up - 1).reshape(-1, L, L)
+    nu = (s != np.roll(s, 1, axis=2)).sum(axis=(1, 2)) + (s != np.roll(s, 1, axis=1)).sum(axis=(1, 2))
+    j = up.sum(axis=1)
+    g = np.zeros((N + 1, N + 1), dtype=np.int64)
+    np.add.at(g, (nu // 2, j), 1)
+    return g
+
+
+def transfer_matrix_ising_em(L: int) -> np.ndarray:
+    """g[k][j] (int64) of the periodic L x L Ising model, L <= 6, by a row transfer matrix.
+
+    State: (first row, current row, unsatisfied bonds so far, up spins so far).  Adding row b
+    after row a adds the horizontal unsatisfied bonds of b, the vertical ones between a and b
+    (popcount(a ^ b)) and popcount(b) up spins; the last row closes onto the first.  Counts stay
+    below 2^36, so float64 matrix products over the previous row are exact."""
+    if L > 6:
+        raise ValueError("(E, M) transfer matrix only for L <= 6")
+    N, R = L * L, 1 << L
+    U, J = 2 * N + 1, N + 1
+    pop = np.array([bin(r).count("1") for r in range(R)])
+    rot = np.array([((r >> 1) | ((r & 1) << (L - 1))) for r in range(R)])
+    hu = np.array([bin(r ^ rot[r]).count("1") for r in range(R)])
+    vd = np.array([[bin(a ^ b).count("1") for b in range(R)] for a in range(R)])
+    T = np.zeros((R, R, U, J))
+    for r0 in range(R):
+        T[r0, r0, hu[r0], pop[r0]] = 1.0
+    for _ in range(L - 1):
+        Tn = np.zeros_like(T)
+        for d in range(L + 1):
+            A = (vd == d).astype(np.float64)                     # A[a, b]
+            S = np.tensordot(T, A, axes=([1], [0]))              # S[z, u, j, b]
+            for b in range(R):
+                du, dj = d + hu[b], pop[b]
+                if du < U and dj < J:
+                    Tn[:, b, du:, dj:] += S[:, :U - du, :J - dj, b]
+        T = Tn
+    g = np.zeros((N + 1, N + 1), dtype=np.int64)
+    for r0 in range(R):
+        for a in range(R):
+            d = vd[a, r0]
+            sub = T[r0, a, :U - d, :]
+            us = np.nonzero(sub.any(axis=1))[0]
+            for u in us:
+                ut = u + d
+                assert ut % 2 == 0
+                g[ut // 2] += np.rint(sub[u]).astype(np.int64)
+    return g
+
+
 def exact_lng(model: int, L: int, q: int = 2) -> tuple:
     """ln g_k over the oracle's bins (tuple of floats, -inf where g = 0)."""
     if model == 0:

@@ -38,6 +38,13 @@
  *           min H * count >= flatness * sum H; latched until the window advances.
  *   advance: ln-domain mean over the m walkers in walker order, H = 0, ln f /= 2.
  *   finished windows freeze ln g and H but keep moving and swapping.
+ *   2D DOS (Sec. 3, Eqs. 3-4; Ising, Q = magnetisation): with the (E, M) measurement on,
+ *           each walker's (bin, up spins) is counted after the moves of every round;
+ *           production rounds continue after every window finished (frozen ln g: a
+ *           multicanonical walk with weight 1/g_w(E) per window).  Fragments
+ *           S_w = mean ln g_w(k) + ln H_w(k,j) - ln sum_j H_w(k,j); adjacent fragments
+ *           join where their unit normals (dS/dE, dS/dM, -1) agree best; Eq. (4) averages
+ *           g where both are present.
  *   swap:   round r pairs windows (w,w+1) with w = r mod 2; Fisher-Yates permutation of the
  *           m partners; ln P = (lg_i[kX]-lg_i[kY]) + (lg_j[kY]-lg_j[kX]).
  *   prep:   from the seeded random state, accept a move iff the distance of k to the window
@@ -121,6 +128,28 @@ double or_lnu(uint32_t w)
     double u = ((double)w + 0.5) * 0x1p-32;
     uint64_t bits;
     memcpy(&bits, &u, 8);
+    int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    uint64_t mb = (bits & 0x000fffffffffffffull) | 0x3ff0000000000000ull;
+    double m;
+    memcpy(&m, &mb, 8);
+    if (m > OR_SQRT2) {
+        m = m * 0.5;
+        e = e + 1;
+    }
+    double s = (m - 1.0) / (m + 1.0);
+    double z = s * s;
+    double p = OR_ATANH_C[11];
+    for (int i = 10; i >= 0; i--) p = fma(p, z, OR_ATANH_C[i]);
+    double r = s * p;
+    r = r + r;
+    return fma((double)e, OR_LN2, r);
+}
+
+/* The same logarithm for any finite x > 0 in the normal range (fragments of g(E, M)). */
+double or_ln(double x)
+{
+    uint64_t bits;
+    memcpy(&bits, &x, 8);
     int e = (int)((bits >> 52) & 0x7ff) - 1023;
     uint64_t mb = (bits & 0x000fffffffffffffull) | 0x3ff0000000000000ull;
     double m;
@@ -295,6 +324,8 @@ typedef struct {
     uint8_t *mode;         /* [h] 0: halving, 1: ln f = 1/t */
     int schedule;          /* 0: f -> sqrt f only, 1: switch to 1/t */
     long long round;
+    uint32_t *hem;         /* [h][W][N+1] (bin, up spins) counts, NULL: not measured */
+    int production;        /* or_rewl_run keeps going after every window finished */
 } or_rewl;
 
 static void *zalloc(size_t n) { return calloc(n ? n : 1, 1); }
@@ -306,6 +337,7 @@ void or_rewl_destroy(or_rewl *r)
     free(r->step); free(r->acc); free(r->pstep); free(r->prep_restarts); free(r->flat);
     free(r->lnf); free(r->iter); free(r->finished); free(r->mask);
     free(r->swap_att); free(r->swap_acc); free(r->it1_round); free(r->mode); free(r->frag);
+    free(r->hem);
     free(r);
 }
 
@@ -583,6 +615,14 @@ void or_rewl_round(or_rewl *r)
             r->k[g] = k;
         }
     }
+    if (r->hem) {
+        for (int g = 0; g < r->nw; g++) {
+            int w = g / r->m, up = 0;
+            const int8_t *sp = r->spins + (size_t)g * N;
+            for (int i = 0; i < N; i++) up += sp[i] > 0;
+            r->hem[((size_t)w * W + (size_t)(r->k[g] - r->lo[w])) * (size_t)(N + 1) + up] += 1u;
+        }
+    }
     for (int w = 0; w < r->h; w++)
         if (!r->finished[w]) check_window(r, w);
     for (int w = (int)(r->round & 1); w + 1 < r->h; w += 2) swap_pair(r, w, r->round);
@@ -594,7 +634,7 @@ long long or_rewl_run(or_rewl *r, long long max_rounds)
 {
     long long n = 0;
     while (n < max_rounds) {
-        int done = 1;
+        int done = !r->production;
         for (int w = 0; w < r->h; w++) done &= r->finished[w];
         if (done) break;
         or_rewl_round(r);
@@ -741,5 +781,143 @@ int or_stitch(int h, int W, int B, const int *lo, const int *hi, const double *l
         double c = out[b0] - norm_target;
         for (int b = 0; b <= B; b++) if (out[b] > -INFINITY) out[b] -= c;
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Joint density of states g(E, M) (Sec. 3, Eqs. 3-4), Ising only.      */
+/* ------------------------------------------------------------------ */
+int or_rewl_measure_em(or_rewl *r, int on)
+{
+    free(r->hem);
+    r->hem = NULL;
+    if (!on) return 0;
+    if (r->model != 0) return -1;
+    r->hem = (uint32_t *)zalloc(sizeof(uint32_t) * (size_t)r->h * r->W * (size_t)(r->N + 1));
+    return 0;
+}
+
+void or_rewl_set_production(or_rewl *r, int on) { r->production = on; }
+
+int or_rewl_get_hem(const or_rewl *r, uint32_t *out)
+{
+    if (!r->hem) return -1;
+    memcpy(out, r->hem, sizeof(uint32_t) * (size_t)r->h * r->W * (size_t)(r->N + 1));
+    return 0;
+}
+
+/* Fragments: S[w][b][j] = mean[w][b] + ln H[w][b][j] - ln sum_j H[w][b][j] where bin b of
+ * window w is valid and H > 0, else -INFINITY.  Rows b >= hi-lo+1 are -INFINITY. */
+void or_frag_em(int h, int W, int N1, const int *lo, const int *hi, const double *mean,
+                const uint8_t *valid, const uint32_t *hem, double *S)
+{
+    for (int w = 0; w < h; w++)
+        for (int b = 0; b < W; b++) {
+            const uint32_t *row = hem + ((size_t)w * W + b) * N1;
+            double *out = S + ((size_t)w * W + b) * N1;
+            uint64_t tot = 0;
+            for (int j = 0; j < N1; j++) tot += row[j];
+            int ok = b <= hi[w] - lo[w] && valid[(size_t)w * W + b] && tot > 0;
+            double lt = ok ? or_ln((double)tot) : 0.0;
+            for (int j = 0; j < N1; j++)
+                out[j] = (ok && row[j] > 0) ? (mean[(size_t)w * W + b] + or_ln((double)row[j])) - lt
+                                           : -INFINITY;
+        }
+}
+
+/* Derivative of one fragment along an axis at index i (n points, stride st): 5-point stencil
+ * where the four neighbours are present, else 3-point, else none. */
+static int em_deriv(const double *S, int i, int n, int st, double d, double *out)
+{
+    if (i - 2 >= 0 && i + 2 < n && S[(i - 2) * st] > -INFINITY && S[(i - 1) * st] > -INFINITY &&
+        S[(i + 1) * st] > -INFINITY && S[(i + 2) * st] > -INFINITY) {
+        double num = ((-S[(i + 2) * st] + 8.0 * S[(i + 1) * st]) - 8.0 * S[(i - 1) * st]) + S[(i - 2) * st];
+        *out = num / (12.0 * d);
+        return 1;
+    }
+    if (i - 1 >= 0 && i + 1 < n && S[(i - 1) * st] > -INFINITY && S[(i + 1) * st] > -INFINITY) {
+        *out = (S[(i + 1) * st] - S[(i - 1) * st]) / (2.0 * d);
+        return 1;
+    }
+    return 0;
+}
+
+/* Unit-normal gradient of fragment Sw (nb rows x N1 columns) at (b, j): Eq. (3). */
+static int em_grad(const double *Sw, int nb, int N1, int b, int j, double de, double dq,
+                   double *gE, double *gQ)
+{
+    const double *col = Sw + j;            /* column j, stride N1 */
+    const double *row = Sw + (size_t)b * N1;
+    return em_deriv(col, b, nb, N1, de, gE) && em_deriv(row, j, N1, 1, dq, gQ);
+}
+
+/* Joins adjacent fragments (w, w+1) at the point where n_w . n_(w+1) is largest (ties: the
+ * smallest bin, then the smallest j; with no normals in both: the point present in both
+ * nearest to the middle of the overlap rows), shifts window w+1 to agree there with the
+ * already shifted window w, then merges the windows in order with Eq. (4).  out: (B+1) x N1,
+ * -INFINITY where absent; logsumexp(out) == norm_target.  joins: [h-1][2] (bin, j).
+ * Returns 0 or -1 (two adjacent fragments share no point). */
+int or_join_em(int h, int W, int B, int N1, const int *lo, const int *hi, const double *S,
+               double de, double dq, double norm_target, double *out, int *joins)
+{
+    double *shift = (double *)zalloc(sizeof(double) * (size_t)h);
+    for (int w = 0; w + 1 < h; w++) {
+        const double *Sa = S + (size_t)w * W * N1, *Sb = S + (size_t)(w + 1) * W * N1;
+        int nba = hi[w] - lo[w] + 1, nbb = hi[w + 1] - lo[w + 1] + 1;
+        int bk = -1, bj = -1;
+        double best = -INFINITY;
+        for (int k = lo[w + 1]; k <= hi[w]; k++)
+            for (int j = 0; j < N1; j++) {
+                int a = k - lo[w], b = k - lo[w + 1];
+                if (!(Sa[(size_t)a * N1 + j] > -INFINITY && Sb[(size_t)b * N1 + j] > -INFINITY)) continue;
+                double aE, aQ, bE, bQ;
+                if (!em_grad(Sa, nba, N1, a, j, de, dq, &aE, &aQ)) continue;
+                if (!em_grad(Sb, nbb, N1, b, j, de, dq, &bE, &bQ)) continue;
+                double num = (aE * bE + aQ * bQ) + 1.0;
+                double den = sqrt((aE * aE + aQ * aQ) + 1.0) * sqrt((bE * bE + bQ * bQ) + 1.0);
+                double dot = num / den;
+                if (dot > best) { best = dot; bk = k; bj = j; }
+            }
+        if (bk < 0) {
+            int mid2 = lo[w + 1] + hi[w], bestd = 1 << 30;
+            for (int k = lo[w + 1]; k <= hi[w]; k++) {
+                int d = 2 * k - mid2;
+                if (d < 0) d = -d;
+                if (d >= bestd) continue;
+                for (int j = 0; j < N1; j++)
+                    if (Sa[(size_t)(k - lo[w]) * N1 + j] > -INFINITY &&
+                        Sb[(size_t)(k - lo[w + 1]) * N1 + j] > -INFINITY) {
+                        bestd = d; bk = k; bj = j;
+                        break;
+                    }
+            }
+        }
+        if (bk < 0) { free(shift); return -1; }
+        shift[w + 1] = (Sa[(size_t)(bk - lo[w]) * N1 + bj] + shift[w]) - Sb[(size_t)(bk - lo[w + 1]) * N1 + bj];
+        joins[2 * w] = bk;
+        joins[2 * w + 1] = bj;
+    }
+    for (size_t i = 0; i < (size_t)(B + 1) * N1; i++) out[i] = -INFINITY;
+    for (int w = 0; w < h; w++)
+        for (int k = lo[w]; k <= hi[w]; k++)
+            for (int j = 0; j < N1; j++) {
+                double v = S[((size_t)w * W + (k - lo[w])) * N1 + j];
+                if (!(v > -INFINITY)) continue;
+                v = v + shift[w];
+                double *o = out + (size_t)k * N1 + j;
+                if (*o > -INFINITY) {            /* Eq. (4): (g_i + g_j) / 2 */
+                    double mx = *o > v ? *o : v, mn = *o > v ? v : *o;
+                    *o = (mx + log1p(exp(mn - mx))) - OR_LN2;
+                } else {
+                    *o = v;
+                }
+            }
+    free(shift);
+    double mx = -INFINITY;
+    for (size_t i = 0; i < (size_t)(B + 1) * N1; i++) if (out[i] > mx) mx = out[i];
+    double sum = 0.0;
+    for (size_t i = 0; i < (size_t)(B + 1) * N1; i++) if (out[i] > -INFINITY) sum += exp(out[i] - mx);
+    double c = (mx + log(sum)) - norm_target;
+    for (size_t i = 0; i < (size_t)(B + 1) * N1; i++) if (out[i] > -INFINITY) out[i] -= c;
     return 0;
 }

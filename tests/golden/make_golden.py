@@ -27,6 +27,16 @@ def write_lng(name, lng, header):
             f.write(f"{k} {float(v)!r}\n")
 
 
+def write_em(name, g, header):
+    with open(os.path.join(HERE, name), "w") as f:
+        f.write(f"# {header}\n# k j g(k, j) (exact integer; k = E/4 + N/2, j = (M + N)/2; "
+                f"zero entries omitted)\n")
+        for k in range(g.shape[0]):
+            for j in range(g.shape[1]):
+                if g[k, j]:
+                    f.write(f"{k} {j} {int(g[k, j])}\n")
+
+
 def main():
     bf4 = X.brute_force_ising(4)
     assert bf4 == X.kaufman_ising(4) == X.transfer_matrix_ising(4)
@@ -40,6 +50,14 @@ def main():
     p3 = X.brute_force_potts(3, 3)
     assert sum(p3) == 3 ** 9
     write_counts("potts_q3_L3_counts.txt", p3, "2D q=3 Potts 3x3 periodic, enumeration of 3^9 states")
+    em4 = X.brute_force_ising_em(4)
+    assert (em4 == X.transfer_matrix_ising_em(4)).all()
+    em6 = X.transfer_matrix_ising_em(6)
+    assert [int(v) for v in em6.sum(axis=1)] == X.transfer_matrix_ising(6)
+    assert (em6 == em6[:, ::-1]).all()
+    write_em("ising_L6_em_counts.txt", em6,
+             "2D Ising 6x6 periodic, joint g(E, M) by the (E, M) transfer matrix; sums over M "
+             "equal the 1D transfer matrix, symmetric under M -> -M")
     for L in (16, 32, 64):
         g = X.kaufman_ising(L)
         assert sum(g) == 2 ** (L * L)
