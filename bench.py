@@ -168,14 +168,48 @@ def whole_job_rate(per_rank_units, world, rank_ms):
 
 
 # ----------------------------------------------------------------------------- main arms
-def _roofline(per_launch_attempts, move_ms, move_launches, sms, step_ms):
+KERNEL_SOURCES = ["paper_1402_2328_gb300/csrc/rewl_kernels.cu",
+                  "paper_1402_2328_gb300/csrc/rewl_kernels.cuh",
+                  "paper_1402_2328_gb300/csrc/rewl_device.cuh"]
+
+
+def kernel_source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes (read + write) per move launch from the committed ncu summary of this
+    workload, when it was captured from the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"k_move_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        t = line.strip().lstrip("-* ").replace("`", "")
+        for key in ("traffic_bytes_per_launch", "kernel_source_digest"):
+            if t.startswith(key + ":"):
+                vals[key] = t.split(":", 1)[1].strip()
+    if vals.get("kernel_source_digest") != kernel_source_digest():
+        return None
+    try:
+        return int(float(vals["traffic_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+def _roofline(per_launch_attempts, move_ms, move_launches, sms, step_ms, workload=None):
     peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tinst = sms * 128 * sm_max_mhz * 1e6 / 1e12
     move_avg_s = (move_ms / max(move_launches, 1)) / 1e3
     achieved = ALG_INSTR_PER_ATTEMPT * per_launch_attempts / move_avg_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
-            "frac": achieved / peak_tinst, "traffic": None, "kernel": "k_move",
+            "frac": achieved / peak_tinst,
+            "traffic": recorded_traffic(workload) if workload else None, "kernel": "k_move",
             "kernel_ms_avg": move_avg_s * 1e3,
             "kernel_share_of_step": move_ms / step_ms if step_ms else None,
             "alg_inst_per_attempt": ALG_INSTR_PER_ATTEMPT,
@@ -256,7 +290,7 @@ def run_gpu_batch(args, wl, rank, world):
                    "autotune_ms_per_round": trial,
                    "parallelism": f"replicas{world}" if world > 1 else "1gpu",
                    "l2": "flushed (256 MB write) before every timed step"},
-        "roofline": _roofline(per_round, move_ms, move_launches, sms, step_ms),
+        "roofline": _roofline(per_round, move_ms, move_launches, sms, step_ms, args.workload),
         "one_at_a_time": {"value": per_round * args.steps / (solo_ms / 1e3), "unit": UNIT,
                           "ms_per_step": solo_ms / args.steps},
         "e2e": {"value": attempts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -378,10 +412,13 @@ def run_warm(args):
     t_fit = time.perf_counter() - t1
     lng_pred = WM.predict_lng(P, args.warm_model, args.warm_L)
 
-    def target(seed, kind):
+    def target(seed, variant):
+        # variant: kind[@ln f0], kind in warm (learned windows), warm_eq, cold, cold_lw
+        kind, _, lnf0 = variant.partition("@")
         if kind.startswith("warm"):
             r = WM.warm_handle(args.warm_model, args.warm_L, args.warm_windows, args.warm_walkers,
-                               args.warm_lnf_final, seed, lng_pred, lnf_init=args.warm_lnf_init)
+                               args.warm_lnf_final, seed, lng_pred,
+                               lnf_init=float(lnf0) if lnf0 else args.warm_lnf_init)
         else:
             r = R.REWL(args.warm_model, args.warm_L, args.warm_windows, 0.75, args.warm_walkers,
                        args.warm_lnf_final, 0.8, seed=seed, interval=10_000)
@@ -402,6 +439,20 @@ def run_warm(args):
         results[kind], lngs[kind] = target(seed_for(5, 1), kind)
     cold = results.get("cold")
     warm = results.get("warm")
+    for v, res in results.items():
+        if cold and res.get("status") == "done" and cold["status"] == "done":
+            res["time_vs_cold"] = res["seconds"] / cold["seconds"]
+        if lngs.get(v) is not None and lngs.get("cold") is not None and v != "cold":
+            a, c_ = lngs[v], lngs["cold"]
+            fin = np.isfinite(a) & np.isfinite(c_)
+            res["max_abs_dlng_vs_cold"] = float(np.max(np.abs(a[fin] - c_[fin])))
+        ex_g = exact_lng_golden(args.warm_model, args.warm_L)
+        if lngs.get(v) is not None and ex_g is not None:
+            ex_a = np.array(ex_g)
+            f2 = np.isfinite(ex_a)
+            ex_a = ex_a - (ex_a[f2].max() + math.log(np.exp(ex_a[f2] - ex_a[f2].max()).sum())
+                           - args.warm_L ** 2 * math.log(2))
+            res["max_abs_dlng_vs_exact"] = float(np.max(np.abs(lngs[v][f2] - ex_a[f2])))
     lng_cold, lng_warm = lngs.get("cold"), lngs.get("warm")
 
     def maxdiff(a, b_):
@@ -432,6 +483,52 @@ def run_warm(args):
         "max_abs_dlng_warm_vs_cold": maxdiff(lng_warm, lng_cold),
         "max_abs_dlng_prediction_vs_cold": maxdiff(pred_n, lng_cold),
     }}
+
+
+def run_em(args):
+    """Joint g(E, M) of the Ising model (Sec. 3, Eqs. 3-4): REWL to ln f_final, then production
+    rounds (frozen ln g, multicanonical per window) with and without the (E, M) measurement, and
+    the normal-vector join; for L = 6 the error against the exact g(E, M) (golden file)."""
+    import numpy as np
+    import torch
+    import paper_1402_2328_gb300.rewl as R
+
+    torch.cuda.set_device(0)
+    L, h, m, K = args.em_L, args.em_windows, args.em_walkers, args.em_rounds
+    r = R.REWL(0, L, h, 0.75, m, args.em_lnf_final, 0.8, seed=seed_for(7), interval=10_000)
+    t0 = time.perf_counter()
+    status = r.run(max_seconds=args.max_seconds)
+    t_conv = time.perf_counter() - t0
+    r.set_param("production", 1)
+    t0 = time.perf_counter()
+    r.run(max_rounds=K)
+    t_plain = time.perf_counter() - t0
+    r.set_param("measure_em", 1)
+    t0 = time.perf_counter()
+    r.run(max_rounds=K)
+    t_meas = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    out, joins = r.stitch_em()
+    t_join = time.perf_counter() - t0
+    res = {"workload": f"ising_L{L}_h{h}_m{m}", "lnf_final": args.em_lnf_final, "status": status,
+           "seconds_to_lnf_final": t_conv, "production_rounds": K,
+           "ms_per_round_plain": t_plain * 1e3 / K, "ms_per_round_measured": t_meas * 1e3 / K,
+           "seconds_join": t_join, "points_present": int(np.isfinite(out).sum()),
+           "joins": joins.tolist()}
+    path = os.path.join(ROOT, "tests", "golden", f"ising_L{L}_em_counts.txt")
+    if os.path.exists(path):
+        N = L * L
+        ex = np.full((N + 1, N + 1), -np.inf)
+        for line in open(path):
+            if not line.startswith("#"):
+                k, j, v = line.split()
+                ex[int(k), int(j)] = math.log(int(v))
+        fin = np.isfinite(ex) & np.isfinite(out)
+        d = np.abs(out[fin] - ex[fin])
+        res.update(max_abs_dlng_vs_exact=float(d.max()), mean_abs_dlng_vs_exact=float(d.mean()),
+                   points_exact=int(np.isfinite(ex).sum()))
+    r.close()
+    return {"em": res}
 
 
 def run_speedup(args):
@@ -611,6 +708,13 @@ def main():
     ap.add_argument("--warm-lnf-init", type=float, default=1e-3)
     ap.add_argument("--train-lnf-final", type=float, default=1e-6)
     ap.add_argument("--train-steps", type=int, default=6000)
+    ap.add_argument("--em", action="store_true",
+                    help="joint g(E, M): production rounds with the (E, M) measurement + join")
+    ap.add_argument("--em-L", type=int, default=32)
+    ap.add_argument("--em-windows", type=int, default=16)
+    ap.add_argument("--em-walkers", type=int, default=8)
+    ap.add_argument("--em-lnf-final", type=float, default=1e-6)
+    ap.add_argument("--em-rounds", type=int, default=2000)
     ap.add_argument("--speedup", action="store_true",
                     help="speed-up s_o(h, m) of Eq. (5) with equal and run-time balanced windows")
     ap.add_argument("--speedup-model", type=int, default=0)
@@ -620,7 +724,8 @@ def main():
     ap.add_argument("--speedup-seeds", type=int, default=8)
     ap.add_argument("--speedup-interval", type=int, default=10_000)
     ap.add_argument("--warm-variants", default="cold,warm",
-                    help="comma list of cold | warm | cold_lw | warm_eq (lw: learned windows)")
+                    help="comma list of cold | warm | cold_lw | warm_eq (lw: learned windows), "
+                         "each optionally @ln_f0, e.g. warm_eq@0.01")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -637,6 +742,9 @@ def main():
         return
     if args.speedup:
         print(json.dumps(run_speedup(args)))
+        return
+    if args.em:
+        print(json.dumps(run_em(args)))
         return
 
     if args.impl == "reference":

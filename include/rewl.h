@@ -78,6 +78,14 @@ int rewl_create(rewl_t *out, int model, int L, int windows, double overlap,
  * where the m walkers' ln g are averaged, without a flatness test), "profile" (1 = time
  * move-kernel launches with CUDA events,
  * see rewl_kernel_time; may be changed at any time).  Unknown key or bad value: INVALID_ARG.
+ * Two keys may also be set after rewl_init (they drop the cached CUDA graph):
+ * "production" (1 = rounds continue after every window finished: ln g and H stay frozen, the
+ * walkers keep moving and exchanging, so every window performs a multicanonical walk with
+ * weight 1/g_w(E) -- the production run of Sec. 3; rewl_run then ends only at max_rounds /
+ * max_seconds; 0 = back to the normal end test) and "measure_em" (Ising only; 1 = allocate and
+ * zero an (E, M) histogram of h x W x (N+1) uint32 and, after the moves of every round, count
+ * each walker's (bin, number of up spins) in its window; 0 = free it; INVALID_ARG when
+ * h W (N+1) > 2^30 or (B+1)(N+1) > 2^28).  The histogram is not part of checkpoints.
  */
 int rewl_set_param(rewl_t r, const char *key, double value);
 
@@ -126,8 +134,9 @@ int rewl_set_stream(rewl_t r, void *stream);
 /*
  * rewl_init -- seeded random lattices (Ising +-1 / Potts 0..q-1 from Philox), then every
  * walker is driven into its window: single-site moves accepted iff the distance of k to
- * the window does not grow; after prep_budget sweeps a walker restarts from the ordered
- * state.  REWL_ERR_PREP if a walker cannot reach its window.  Called by rewl_run if needed.
+ * the window does not grow; after prep_budget sweeps a walker restarts once from the ground
+ * state (all +1 / all 0), or from the checkerboard (+1/-1, 0/1) when 2 lo > B.  REWL_ERR_PREP if
+ * a walker cannot reach its window.  Called by rewl_run if needed.
  */
 int rewl_init(rewl_t r);
 
@@ -243,6 +252,39 @@ void rewl_destroy(rewl_t r);
 
 /* Message for the last error of r (or of a failed rewl_create / free function if r = NULL). */
 const char *rewl_last_error(rewl_t r);
+
+/*
+ * Joint density of states g(E, Q) with Q = magnetisation M of the Ising model (Sec. 3,
+ * Eqs. 3-4).  Bins: k as in rewl_get_lng, j = number of up spins = (M + N)/2 in [0, N].
+ *
+ * rewl_get_hist_em -- the (E, M) histogram (host, bytes == h*W*(N+1)*4): [w][k - lo_w][j].
+ * STATE if "measure_em" is off.
+ */
+int rewl_get_hist_em(rewl_t r, uint32_t *out, size_t bytes);
+/*
+ * rewl_stitch_em -- g(E, M) from the measured fragments: for every window w the fragment
+ * S_w(k, j) = mean ln g_w(k) + ln H_w(k, j) - ln sum_j H_w(k, j) (absent where H_w = 0 or the bin
+ * is unvisited), then rewl_join_em with dE = 4 per bin, dM = 2 per up spin, normalised to
+ * sum g = 2^N.  out: host, n >= (B+1)(N+1) values, row-major [k][j], -INFINITY where absent.
+ * joins: host, 2(h-1) ints (may be NULL).  Blocks until done.
+ */
+int rewl_stitch_em(rewl_t r, double *out, size_t n, int *joins);
+/*
+ * rewl_join_em -- joins 2D fragments (Sec. 3, Eqs. 3-4).  S: device, [h][W][N1] float64,
+ * fragment w's row b is bin lo_w + b (rows past hi_w - lo_w ignored), -INFINITY = absent.
+ * For each adjacent pair (w, w+1) the unit normals n = (dS/dE, dS/dQ, -1)/|.| (5-point stencil
+ * along an axis where the four neighbours are present, else 3-point; de, dq = physical step per
+ * bin and per j) are compared at every point of the overlap present in both with a normal in
+ * both; the join point maximises n_w . n_(w+1) (ties: smallest bin, then smallest j; with no
+ * such point: the point present in both nearest to the middle of the overlap rows).  Window
+ * w+1 is shifted to agree there with the already shifted window w; the windows are merged in
+ * order with Eq. (4): where both are present g = (g_i + g_j)/2.  out: device, (B+1) x N1,
+ * normalised to logsumexp(out) = norm_target.  lo_hi: host, 2h ints (lo[], then hi[]; windows
+ * as in rewl_set_windows).  joins: host, 2(h-1) ints (bin, j) or NULL.  NOT_CONVERGED when
+ * two adjacent fragments share no point.  Scratch is allocated and freed inside; blocks.
+ */
+int rewl_join_em(const double *S, int h, int W, int B, int N1, const int *lo_hi, double de,
+                 double dq, double norm_target, double *out, int *joins, void *stream);
 
 /*
  * Batched instances.  Many independent REWL simulations (any mix of models, L, window

@@ -37,6 +37,9 @@
  *   flat:   every swap interval; over the bins any walker of the window ever visited;
  *           min H * count >= flatness * sum H; latched until the window advances.
  *   advance: ln-domain mean over the m walkers in walker order, H = 0, ln f /= 2.
+ *   prep:   from the seeded random lattice, single-site moves accepted iff the distance of
+ *           k to the window does not grow; after prep_budget sweeps one restart from the
+ *           ground state (or, for a window in the upper half of the bins, the checkerboard).
  *   finished windows freeze ln g and H but keep moving and swapping.
  *   2D DOS (Sec. 3, Eqs. 3-4; Ising, Q = magnetisation): with the (E, M) measurement on,
  *           each walker's (bin, up spins) is counted after the moves of every round;
@@ -455,8 +458,15 @@ int or_rewl_init(or_rewl *r)
             uint64_t budget = (uint64_t)r->prep_budget * (uint64_t)N;
             for (int phase = 0; phase < 2 && dist_to(k, lo, hi) > 0; phase++) {
                 if (phase == 1) {
-                    for (int j = 0; j < N; j++) s[j] = is_ising(r->model) ? 1 : 0;
-                    k = 0;
+                    /* restart from the ordered state nearer the window: the ground state, or
+                     * for a window in the upper half of the bins the checkerboard (every bond
+                     * unsatisfied for even L) */
+                    int top = 2 * lo > r->B;
+                    for (int j = 0; j < N; j++) {
+                        int odd = top && (((j % r->L) + (j / r->L)) & 1);
+                        s[j] = is_ising(r->model) ? (odd ? -1 : 1) : (odd ? 1 : 0);
+                    }
+                    k = top ? or_bin_of_energy(r->model, N, or_energy(r->model, r->L, s)) : 0;
                     r->prep_restarts[g]++;
                 }
                 uint64_t end = ps + budget;

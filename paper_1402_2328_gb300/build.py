@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librewl.so")
-SOURCES = ["rewl_kernels.cu", "rewl_host.cu", "rewl_batch.cu", "rewl_mlp.cu"]
+SOURCES = ["rewl_kernels.cu", "rewl_host.cu", "rewl_batch.cu", "rewl_mlp.cu", "rewl_em.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

@@ -48,9 +48,9 @@ __device__ __forceinline__ uint32_t mulhi(uint32_t a, uint32_t b) { return __umu
 // u = m 2^e with m in [sqrt(1/2), sqrt(2)), ln u = e ln2 + 2 atanh(s), s = (m-1)/(m+1),
 // atanh(s) = s (1 + z/3 + z^2/5 + ... + z^11/23), z = s^2 <= 0.0295.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ double lnu64(uint32_t w)
+__device__ __forceinline__ double ln64(double u)
 {
-    const double u = __dmul_rn(__dadd_rn((double)w, 0.5), 0x1p-32);
+    // u > 0 in the normal range (random numbers, histogram counts and their sums)
     const long long bits = __double_as_longlong(u);
     int e = (int)((bits >> 52) & 0x7ff) - 1023;
     double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
@@ -75,6 +75,11 @@ __device__ __forceinline__ double lnu64(uint32_t w)
     double r = __dmul_rn(s, p);
     r = __dadd_rn(r, r);
     return __fma_rn((double)e, 0x1.62e42fefa39efp-1, r);
+}
+
+__device__ __forceinline__ double lnu64(uint32_t w)
+{
+    return ln64(__dmul_rn(__dadd_rn((double)w, 0.5), 0x1p-32));
 }
 
 // float32 screening value of ln u (hardware log2 approximation).  Its largest distance

@@ -19,7 +19,7 @@ struct rewl_s {
     uint64_t seed = 0;
     uint32_t inst = 0;
     long long interval = 10000, prep_budget = 100;
-    int graph_rounds = 32, wpb = 0, check_all = 0, profile = 0, schedule = 0;
+    int graph_rounds = 32, wpb = 0, check_all = 0, profile = 0, schedule = 0, production = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free; // move-kernel timing
     std::vector<int> lo, hi;
     std::vector<double> lng_init;

@@ -95,7 +95,8 @@ static void release(rewl_t r)
     State &s = r->st;
     void *ptrs[] = {s.spins, s.cfg, s.k, s.lng, s.H, s.step, s.acc, s.pstep, s.restarts, s.flat,
                     r->d_lohi, s.lnf, s.iter, s.finished, s.mask, s.swap_att, s.swap_acc,
-                    s.it1_round, s.mode, s.frag, s.status, r->d_mean, r->d_out, r->d_joins, r->d_ok};
+                    s.it1_round, s.mode, s.frag, s.hem, s.status, r->d_mean, r->d_out, r->d_joins,
+                    r->d_ok};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (r->h_status) cudaFreeHost(r->h_status);
@@ -118,6 +119,7 @@ static int allocate(rewl_t r)
     cudaError_t e = cudaSuccess;
     const size_t nw = (size_t)r->nw, W = (size_t)r->W, h = (size_t)r->h;
     s.model = r->model;
+    s.production = r->production;
     s.q = r->q;
     s.L = r->L;
     s.N = r->N;
@@ -223,6 +225,38 @@ int rewl_set_param(rewl_t r, const char *key, double v)
     const std::string k(key);
     if (k == "profile" && (v == 0 || v == 1)) {
         r->profile = (int)v;
+        return REWL_OK;
+    }
+    if (k == "production" && (v == 0 || v == 1)) {
+        r->production = (int)v;
+        r->st.production = (int)v;
+        if (r->graph) cudaGraphExecDestroy(r->graph);
+        r->graph = nullptr;
+        if (r->inited) { // re-evaluate "every window finished" under the new rule
+            cudaError_t e = launch_set_done(r->st, r->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+            if (e != cudaSuccess) return r->cuda_fail(e, "rewl_set_param(production)");
+        }
+        return REWL_OK;
+    }
+    if (k == "measure_em" && (v == 0 || v == 1)) {
+        if (r->model != 0) return r->fail(REWL_ERR_INVALID_ARG, "measure_em: Ising model only");
+        if (!r->allocated) return r->fail(REWL_ERR_STATE, "measure_em: no state");
+        const size_t N1 = (size_t)r->N + 1;
+        if ((size_t)r->h * r->W * N1 > (1u << 30) || (size_t)(r->B + 1) * N1 > (1u << 28))
+            return r->fail(REWL_ERR_INVALID_ARG, "measure_em: lattice too large for the (E, M) grid");
+        if (r->graph) cudaGraphExecDestroy(r->graph);
+        r->graph = nullptr;
+        cudaError_t e = cudaStreamSynchronize(r->stream);
+        if (r->st.hem) cudaFree(r->st.hem);
+        r->st.hem = nullptr;
+        if (v == 1 && e == cudaSuccess) {
+            const size_t bytes = (size_t)r->h * r->W * N1 * 4u;
+            e = cudaMalloc(&r->st.hem, bytes);
+            if (e == cudaSuccess) e = cudaMemsetAsync(r->st.hem, 0, bytes, r->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+        }
+        if (e != cudaSuccess) return r->cuda_fail(e, "rewl_set_param(measure_em)");
         return REWL_OK;
     }
     if (r->inited) return r->fail(REWL_ERR_STATE, "rewl_set_param after rewl_init");
@@ -367,6 +401,7 @@ cudaError_t rewl_enqueue_round(rewl_t r)
         e = cudaEventRecord(ev.second, r->stream);
         r->ev_used.push_back(ev);
     }
+    if (e == cudaSuccess && r->st.hem) e = launch_measure_em(r->st, r->stream);
     if (e == cudaSuccess) e = launch_check(r->st, r->flatness, r->lnf_final, r->stream);
     if (e == cudaSuccess) e = launch_swap(r->st, r->stream);
     if (e == cudaSuccess) e = launch_round_end(r->st, r->stream);

@@ -102,16 +102,20 @@ __device__ __forceinline__ float warp_maxf(float v)
     return v;
 }
 
-// Float64 decision from the exact values (rare).  All lanes take part.
-__device__ __noinline__ bool exact_decision(const double *glng, const uint32_t *gH,
-                                            const uint32_t *Hs, int lo, int k, int kp, int k0,
-                                            int cnt, double lnf, bool frozen, uint32_t w2)
+// visits of bin b since the launch started: the shadow grew by lnfq per visit
+__device__ __forceinline__ uint32_t visits(const long long *V, const double *glng, int b, long long lnfq)
 {
-    const int ck = __shfl_sync(FULL, cnt, (k - k0 + 16) & 31);
-    const int ckp = __shfl_sync(FULL, cnt, (kp - k0 + 16) & 31);
+    return (uint32_t)((V[b] - __double2ll_rn(__dmul_rn(glng[b], 0x1p32))) / lnfq);
+}
+
+// Float64 decision from the exact values (rare).  All lanes take part.
+__device__ __noinline__ bool exact_decision(const double *glng, const long long *V, int lo, int k,
+                                            int kp, double lnf, long long lnfq, bool frozen,
+                                            uint32_t w2)
+{
     __syncwarp();
-    const uint32_t vk = frozen ? 0u : Hs[k - lo] - gH[k - lo] + (uint32_t)ck;
-    const uint32_t vkp = frozen ? 0u : Hs[kp - lo] - gH[kp - lo] + (uint32_t)ckp;
+    const uint32_t vk = frozen ? 0u : visits(V, glng, k - lo, lnfq);
+    const uint32_t vkp = frozen ? 0u : visits(V, glng, kp - lo, lnfq);
     const double lk = seqadd(glng[k - lo], lnf, vk);
     const double lkp = seqadd(glng[kp - lo], lnf, vkp);
     const double d = __dsub_rn(lk, lkp);
@@ -126,8 +130,9 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
     if (s.status != nullptr && s.status->done) return;
     int8_t *sp = reinterpret_cast<int8_t *>(base);
     long long *V = reinterpret_cast<long long *>(base + pad16(s.N));
-    uint32_t *Hs = reinterpret_cast<uint32_t *>(V + padw(s.W));
-    uint16_t *stamp = reinterpret_cast<uint16_t *>(Hs + padw(s.W)); // [N] batch claims
+    float2 *stage = reinterpret_cast<float2 *>(V + padw(s.W));        // [32] (dk, ln u) of the batch
+    uint32_t *vis = reinterpret_cast<uint32_t *>(stage + 32);         // [W bits] bin visited
+    uint16_t *stamp = reinterpret_cast<uint16_t *>(vis + visw(s.W));  // [N] batch claims
 
     const int w = slot / s.m;
     const int lo = s.lo[w], hi = s.hi[w], nb = hi - lo + 1;
@@ -161,8 +166,21 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         bad = bad || !(fabs(x) < 0x1p30); // also catches NaN
         mx = fmax(mx, fabs(x));
         V[b] = bad ? 0LL : __double2ll_rn(__dmul_rn(x, 0x1p32));
-        Hs[b] = gH[b];
     }
+    // visited bits: bins any walker of the window visited before this launch, plus the ones
+    // this walker visits now (set with every visit below)
+    // (replay has no window mask: every bin counts as visited there)
+    const uint8_t *gmask = s.mask ? s.mask + (size_t)w * s.W : nullptr;
+    for (int i = lane; i < visw(s.W); i += 32) {
+        uint32_t bits = 0u;
+        for (int j = 0; j < 32; ++j) {
+            const int b = 32 * i + j;
+            if (b < nb && (gmask == nullptr || gmask[b])) bits |= 1u << j;
+        }
+        vis[i] = bits;
+    }
+    __syncwarp();
+    if (lane == 0) vis[(k - lo) >> 5] |= 1u << ((k - lo) & 31); // the start bin
     mx = warp_max(mx);
     if (__any_sync(FULL, bad) || !(lnf >= 0x1p-32 && lnf < 0x1p20)) {
         // the int64 shadow would overflow or lose the increment: leave the state untouched
@@ -193,9 +211,17 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
             const long long x = V[bj - lo] - V[k0 - lo];
             Lw = __fmaf_rn(__uint2float_rn((uint32_t)x), 0x1p-32f, (float)(int)(x >> 32));
         }
-        const float Mx = warp_maxf(bin_ok ? fabsf(Lw) : 0.0f) + 33.0f * lnf_f + 0x1p-20f;
+        // largest |Lw| of the cache (non-negative floats order like their bit patterns)
+        // Bins never visited (in the window before this launch, or by this walker now) keep
+        // their initial ln g while the others grow, so their cache values can be far off: they
+        // are marked NaN (a step there is flagged unsure and decided from the float64 values)
+        // and do not widen the float32 margin of every other step.
+        const bool far = bin_ok && !((vis[(bj - lo) >> 5] >> ((bj - lo) & 31)) & 1u);
+        const float Mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(bin_ok && !far ? fabsf(Lw) : 0.0f))) +
+                         33.0f * lnf_f + 0x1p-20f;
         const float M = Mbase + 40.0f * ulpf(2.0f * Mx);
         if (!bin_ok) Lw = INFINITY; // a move there is rejected: ln g(k) - inf < ln u
+        if (far) Lw = __int_as_float(0x7fc00000);
 
         // ---- parallel phase: lane j evaluates proposal t + j on the batch-start lattice
         uint32_t w0, w1, w2;
@@ -223,6 +249,7 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         int snew;
         const int dk = propose_dk<ISING>(sp, lat, s.q, site, pr, snew);
         const float thr = lnu32(w2);
+        stage[lane] = make_float2(__int_as_float(dk), thr);
         // conflict-free prefix: proposal j may be resolved on the batch-start lattice only if
         // no earlier proposal of the batch sits on its site or a neighbour
         // claim stamp = (batch mod 2047) << 5 | lane, written by the lowest lane proposing the site;
@@ -252,14 +279,17 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         // issued together, so one shuffle latency covers two moves.  Decision variable:
         // e = ln g(k) - ln g(k') - thr; accept if e > M, reject if e < -M, else unsure.
         int xk = 16; // cache offset of the current bin
+        int myx = 16; // lane j: cache offset of the bin after step j
         float Lk = 0.0f;
         unsigned accbits = 0u, badbits = 0u, saccbits = 0u, srejbits = 0u;
+        const float4 *stage4 = reinterpret_cast<const float4 *>(stage);
 #pragma unroll
         for (int p = 0; p < 16; ++p) {
             const int i = 2 * p;
             if ((p & 3) == 0 && p > 0 && (badbits != 0u || i >= J)) break;
-            const int dk0 = __shfl_sync(FULL, dk, i), dk1 = __shfl_sync(FULL, dk, i + 1);
-            const float th0 = __shfl_sync(FULL, thr, i), th1 = __shfl_sync(FULL, thr, i + 1);
+            const float4 q = stage4[p]; // (dk, ln u) of steps i and i+1, a broadcast read
+            const int dk0 = __float_as_int(q.x), dk1 = __float_as_int(q.z);
+            const float th0 = q.y, th1 = q.w;
             const int x0 = xk + dk0;       // k' of step i
             const int xA = x0 + dk1;       // k' of step i+1 if step i moved
             const int xR = xk + dk1;       // k' of step i+1 if step i stayed
@@ -271,26 +301,32 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
             const float e0 = (Lk - L0) - th0;
             const bool a0 = dz0 || e0 > M;
             const bool moved0 = a0 && !dz0;
-            const bool un0 = !dz0 && (CHECK ? (L0 < INFINITY) : !(fabsf(e0) > M));
+            const bool un0 = !dz0 && (CHECK ? !(L0 == INFINITY) : !(fabsf(e0) > M));
             const bool bad0 = (unsigned)x0 >= 32u || un0;
-            // step i+1 in the world the first step chose
+            // step i+1, evaluated in both worlds (step i moved / stayed) alongside step i; the
+            // outcome of step i only selects, so the dependency chain per pair is one lookup,
+            // one decision and the selects
             const float LA = (dk1 == -dk0) ? Lk : LA_; // back to the bin just left
             const float Lm = L0 + lnf_f;               // value after step i if moved
             const float Ls = Lk + lnf_f;               // value after step i if stayed
+            const bool dz1 = dk1 == 0;
+            const float eA = (Lm - LA) - th1, eR = (Ls - LR) - th1;
+            const bool aA = dz1 || eA > M, aR = dz1 || eR > M;
             const float Lc1 = moved0 ? Lm : Ls;
             const float L1 = moved0 ? LA : LR;
             const int x1 = moved0 ? xA : xR;
             const int xc1 = moved0 ? x0 : xk;
-            const bool dz1 = dk1 == 0;
-            const float e1 = (Lc1 - L1) - th1;
-            const bool a1 = dz1 || e1 > M;
+            const float e1 = moved0 ? eA : eR;
+            const bool a1 = moved0 ? aA : aR;
             const bool moved1 = a1 && !dz1;
-            const bool un1 = !dz1 && (CHECK ? (L1 < INFINITY) : !(fabsf(e1) > M));
+            const bool un1 = !dz1 && (CHECK ? !(L1 == INFINITY) : !(fabsf(e1) > M));
             const bool bad1 = (unsigned)x1 >= 32u || un1;
             // write back the running values of the bins left
             if (moved0 && lane == xk) Lw = Lk;
             if (moved1 && lane == xc1) Lw = Lc1;
             xk = moved1 ? x1 : xc1;
+            if (lane == i) myx = xc1;
+            if (lane == i + 1) myx = xk;
             Lk = (moved1 ? L1 : Lc1) + lnf_f;
             accbits |= (a0 ? (1u << i) : 0u) | (a1 ? (2u << i) : 0u);
             badbits |= (bad0 ? (1u << i) : 0u) | (bad1 ? (2u << i) : 0u);
@@ -303,15 +339,9 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         const int ndone = stopbits ? __ffs(stopbits) - 1 : 32;
         const bool amb_stop = ndone < J;
         accbits &= ndone >= 32 ? 0xffffffffu : ((1u << ndone) - 1u);
-        // bin after each step: prefix sum of the accepted energy changes
-        int pos = ((accbits >> lane) & 1u) ? dk : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(FULL, pos, o);
-            if (lane >= o) pos += v;
-        }
-        const int mypos = k + pos;
-        const int kc = ndone > 0 ? k + __shfl_sync(FULL, pos, ndone - 1) : k;
+        // bin after each step (valid for the steps done, all inside the cache)
+        const int mypos = k0 - 16 + myx;
+        const int kc = ndone > 0 ? k0 - 16 + __shfl_sync(FULL, myx, ndone - 1) : k0;
         // float32 verdict at the cut (CHECK): 1 sure accept, 0 sure reject, -1 unsure
         const int scr = !CHECK || ndone >= 32 ? -1
                         : (((saccbits >> ndone) & 1u) ? 1 : (((srejbits >> ndone) & 1u) ? 0 : -1));
@@ -319,10 +349,21 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         // ---- side effects of steps 0..ndone-1
         const bool mine = lane < ndone;
         if (mine && ((accbits >> lane) & 1u)) sp[site] = (int8_t)snew; // conflict-free sites
-        if (mine && !frozen) {
-            atomicAdd(&Hs[mypos - lo], 1u);
+        if (mine && !frozen)
             atomicAdd(reinterpret_cast<unsigned long long *>(&V[mypos - lo]),
                       (unsigned long long)lnfq);
+        {   // bins visited by the steps done: one warp OR of cache offsets, one lane writes
+            const uint32_t vm = __reduce_or_sync(FULL, mine ? 1u << myx : 0u);
+            if (lane == 0 && vm) {
+                const int off = k0 - 16 - lo; // bin of cache offset 0, window-local (>= -16)
+                if (off >= 0) {
+                    const unsigned long long v = (unsigned long long)vm << (off & 31);
+                    vis[off >> 5] |= (uint32_t)v;
+                    if (v >> 32) vis[(off >> 5) + 1] |= (uint32_t)(v >> 32);
+                } else {
+                    vis[0] |= vm >> (-off); // offsets below the window are never visited
+                }
+            }
         }
         if (REPLAY && mine) {
             c.acc_out[(size_t)slot * T + t + lane] = (accbits >> lane) & 1u;
@@ -343,7 +384,7 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
             const int kp = k + dki;
             bool acc = dki == 0;
             if (!acc && kp >= lo && kp <= hi) {
-                acc = exact_decision(glng, gH, Hs, lo, k, kp, k0, 0, lnf, frozen, w2i);
+                acc = exact_decision(glng, V, lo, k, kp, lnf, lnfq, frozen, w2i);
                 if (scr < 0) ++nex;
                 else if ((int)acc != scr) ++nmis;
             }
@@ -352,10 +393,8 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
                 k = kp;
                 ++nacc;
             }
-            if (!frozen && lane == 0) {
-                Hs[k - lo] += 1u;
-                V[k - lo] += lnfq;
-            }
+            if (!frozen && lane == 0) V[k - lo] += lnfq;
+            if (lane == 0) vis[(k - lo) >> 5] |= 1u << ((k - lo) & 31);
             if (REPLAY && lane == 0) {
                 c.acc_out[(size_t)slot * T + t] = acc ? 1 : 0;
                 c.dk_out[(size_t)slot * T + t] = dki;
@@ -376,10 +415,10 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
     if (!frozen) {
         double *gl = s.lng + (size_t)slot * s.W;
         for (int b = lane; b < nb; b += 32) {
-            const uint32_t h1 = Hs[b], h0 = gH[b];
-            if (h1 != h0) {
-                gl[b] = seqadd(gl[b], lnf, h1 - h0);
-                gH[b] = h1;
+            const uint32_t v = visits(V, gl, b, lnfq);
+            if (v != 0u) {
+                gl[b] = seqadd(gl[b], lnf, v);
+                gH[b] += v;
             }
         }
     }
@@ -506,9 +545,13 @@ __global__ void k_init_prep(State s, long long prep_budget)
     const unsigned long long budget = (unsigned long long)prep_budget * (unsigned long long)N;
     int restarts = 0;
     for (int phase = 0; phase < 2 && dist_to(k, lo, hi) > 0; ++phase) {
-        if (phase == 1) {
-            for (int j = 0; j < N; ++j) sp[j] = ising ? 1 : 0;
-            k = 0;
+        if (phase == 1) { // restart from the ground state, or the checkerboard for an upper window
+            const bool top = 2 * lo > (ising ? N : 2 * N);
+            for (int j = 0; j < N; ++j) {
+                const bool odd = top && (((j % s.L) + (j / s.L)) & 1);
+                sp[j] = ising ? (int8_t)(odd ? -1 : 1) : (int8_t)(odd ? 1 : 0);
+            }
+            k = top ? bin_of_lattice(sp, s.L, N, ising) : 0;
             ++restarts;
         }
         const unsigned long long end = ps + budget;
@@ -743,7 +786,7 @@ __device__ __forceinline__ void round_end(const State &s)
 {
     if (s.status->done) return;
     s.status->round += 1;
-    int all = 1;
+    int all = !s.production;
     for (int w = 0; w < s.h; ++w) all &= s.finished[w];
     if (all) s.status->done = 1;
 }
@@ -771,7 +814,7 @@ cudaError_t launch_round_end(const State &s, cudaStream_t st)
 
 __global__ void k_set_done(State s)
 {
-    int all = 1;
+    int all = !s.production;
     for (int w = 0; w < s.h; ++w) all &= s.finished[w];
     s.status->done = all;
 }

@@ -43,6 +43,8 @@ struct State {
     uint8_t *mode;            // [h] 0: ln f halving, 1: ln f = 1/t
     int schedule;             // 0: halving only, 1: switch to 1/t
     double *frag;             // [nw][W] ln g of each walker just before its window's last average
+    uint32_t *hem;            // [h][W][N+1] (bin, up spins) counts, nullptr: not measured
+    int production;           // rounds continue after every window finished
     DevStatus *status;
     uint32_t key0, key1, inst;
 };
@@ -56,11 +58,16 @@ struct MoveCfg {
     int *acc_out, *dk_out;  // replay: [nw][T]
 };
 
+// 32-bit words of the per-walker visited-bin bit set (padded to 16 bytes)
+__host__ __device__ inline int visw(int W) { return (((W + 31) >> 5) + 3) & ~3; }
+
 // Shared memory of one walker in the move kernel: lattice (16-byte padded), int64 ln g
-// shadow and uint32 H over the window (padded to 4 bins), uint16 claim stamps per site.
+// shadow over the window (padded to 4 bins; the visit counts are recovered from it), the
+// batch's (dk, ln u) staging (32 x 8 bytes), the visited-bin bit set, uint16 claim stamps.
 __host__ __device__ inline size_t move_smem_per_walker(int N, int W)
 {
-    return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 12u + (size_t)((N + 7) & ~7) * 2u;
+    return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 8u + 256u + (size_t)visw(W) * 4u +
+           (size_t)((N + 7) & ~7) * 2u;
 }
 cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st);
 // Batched instances: states/jobs/tables are device arrays (see the kernels).
@@ -75,6 +82,8 @@ cudaError_t launch_check(const State &s, double flatness, double lnf_final, cuda
 cudaError_t launch_swap(const State &s, cudaStream_t st);
 cudaError_t launch_round_end(const State &s, cudaStream_t st);
 cudaError_t launch_set_done(const State &s, cudaStream_t st);
+// joint density of states g(E, M) (rewl_em.cu)
+cudaError_t launch_measure_em(const State &s, cudaStream_t st);
 cudaError_t launch_window_mean(const State &s, double *out /*[h][W]*/, cudaStream_t st);
 cudaError_t launch_stitch(const State &s, const double *mean, double de, int step, int norm,
                           double target, double *out /*B+1*/, int *joins /*h-1*/,

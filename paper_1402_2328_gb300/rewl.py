@@ -7,6 +7,7 @@ is not built, ``lib()`` raises: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 
 import numpy as np
@@ -71,6 +72,9 @@ def lib():
             "rewl_windows_balanced": ([P, I, I, D, P], I),
             "rewl_thermo": ([P, I, I, P, I, P, P, P], I),
             "rewl_jackknife": ([P, P, I, I], I),
+            "rewl_get_hist_em": ([P, P, C.c_size_t], I),
+            "rewl_stitch_em": ([P, P, C.c_size_t, P], I),
+            "rewl_join_em": ([P, I, I, I, I, P, D, D, D, P, P, P], I),
             "rewl_balanced_from_prerun": ([P, I, D, P], I),
             "rewl_balanced_scaled": ([P, I, I, D, P], I),
             "rewl_mlp_forward": ([P, P, P, I, P], I),
@@ -270,6 +274,19 @@ class REWL:
         _check(self._lib.rewl_stitch(self._h, _ptr(out), len(out), norm, _ptr(joins)), self._h)
         return out, joins[: self.h - 1]
 
+    def hist_em(self) -> np.ndarray:
+        """(E, M) histogram [h][W][N+1] (parameter "measure_em" must be on)."""
+        out = np.zeros((self.h, self.W, self.N + 1), np.uint32)
+        _check(self._lib.rewl_get_hist_em(self._h, _ptr(out), out.nbytes), self._h)
+        return out
+
+    def stitch_em(self):
+        """Joint ln g(E, M), (B+1) x (N+1) (-inf where absent), and the join points [h-1][2]."""
+        out = np.zeros((self.B + 1, self.N + 1), np.float64)
+        joins = np.zeros((max(self.h - 1, 1), 2), np.int32)
+        _check(self._lib.rewl_stitch_em(self._h, _ptr(out), out.size, _ptr(joins)), self._h)
+        return out, joins[: self.h - 1]
+
     def jackknife(self, norm: int = 0):
         """Per-bin jackknife error of the joined ln g (NaN where a resample has no value)."""
         out = np.zeros(self.B + 1, np.float64)
@@ -394,6 +411,19 @@ def thermo(lng, model, L, T, U, C, stream=None):
     """u(T) = <E>/N and c(T) from ln g (device tensors)."""
     _check(lib().rewl_thermo(_ptr(lng), int(model), int(L), _ptr(T), T.numel(), _ptr(U), _ptr(C),
                              _stream_ptr(stream)))
+
+
+def join_em(S, lo, hi, B: int, out, de: float = 4.0, dq: float = 2.0, norm_target=None,
+            stream=None):
+    """Joins 2D fragments S (CUDA float64 [h][W][N1]) into out (CUDA float64 [B+1][N1]);
+    norm_target defaults to (N1-1) ln 2.  Returns the join points [h-1][2] (bin, j)."""
+    h, W, N1 = S.shape
+    lohi = np.ascontiguousarray(np.concatenate([lo, hi]), np.int32)
+    joins = np.zeros((max(h - 1, 1), 2), np.int32)
+    tgt = (N1 - 1) * math.log(2.0) if norm_target is None else float(norm_target)
+    _check(lib().rewl_join_em(_ptr(S), int(h), int(W), int(B), int(N1), _ptr(lohi), float(de),
+                              float(dq), tgt, _ptr(out), _ptr(joins), _stream_ptr(stream)))
+    return joins[: h - 1]
 
 
 def windows_balanced(cost, h: int, overlap: float = 0.75):

@@ -125,6 +125,8 @@ def _replay_inputs(model, L, n, T, W, seed, scale):
     hi = np.minimum(B, lo + width).astype(np.int32)  # k <= hi, hi - lo + 1 <= W
     lng = I.random_lng(rng, n, W, scale=scale)
     lng += rng.choice([-50.0, 0.0, 100.0, 3000.0], size=(n, 1))
+    if scale >= 5.0:  # steep rows with spikes: many cached bins beyond the float32 cap
+        lng += np.where(rng.random((n, W)) < 0.1, 500.0, 0.0)
     H = I.random_H(rng, n, W)
     lnf = np.where(rng.random(n) < 0.6, 2.0 ** -rng.integers(0, 27, n), rng.uniform(1e-6, 0.5, n))
     frozen = (rng.random(n) < 0.1).astype(np.uint8)
@@ -135,7 +137,8 @@ def _replay_inputs(model, L, n, T, W, seed, scale):
 @pytest.mark.parametrize("model,L,n,T,W,scale", [
     (0, 4, 300, 1, 12, 0.8), (0, 8, 300, 64, 40, 0.5), (0, 7, 200, 45, 40, 0.5),
     (0, 64, 128, 200, 64, 0.3), (3, 5, 300, 33, 40, 0.5), (10, 12, 200, 100, 80, 0.4),
-    (2, 6, 100, 70, 60, 0.5), (10, 40, 64, 300, 64, 0.2)])
+    (2, 6, 100, 70, 60, 0.5), (10, 40, 64, 300, 64, 0.2), (0, 16, 200, 150, 60, 6.0),
+    (10, 12, 200, 150, 80, 8.0)])
 def test_replay_bit_exact(cuda_lib, model, L, n, T, W, scale):
     spins, k, lo, hi, lng, H, lnf, frozen, words = _replay_inputs(model, L, n, T, W, 7 + L + model, scale)
     q = 2 if model == 0 else model
@@ -272,12 +275,16 @@ def test_caller_windows_bit_exact():
     import paper_1402_2328_gb300.rewl as R
     cost = np.ones(257)
     cost[:60] = 8.0
+    top = (np.array([0, 200, 240, 250]), np.array([210, 245, 252, 256]))  # prep restarts
     for model, L, h, m, lohi in [(0, 16, 6, 2, R.windows_balanced(cost, 6, 0.75)),
-                                 (3, 8, 4, 3, R.windows_balanced(np.linspace(4, 1, 129), 4, 0.75))]:
+                                 (3, 8, 4, 3, R.windows_balanced(np.linspace(4, 1, 129), 4, 0.75)),
+                                 (0, 16, 4, 3, top)]:
         lo, hi = lohi
-        g = R.REWL(model, L, h, 0.75, m, 1e-4, 0.8, seed=9 + model, interval=700)
+        pb = 2 if lohi is top else 100
+        g = R.REWL(model, L, h, 0.75, m, 1e-4, 0.8, seed=9 + model, interval=700, prep_budget=pb)
         g.set_windows(lo, hi)
-        o = O.REWL(model, L, h, 0.75, m, 1e-4, 0.8, seed=9 + model, interval=700, lo_hi=(lo, hi))
+        o = O.REWL(model, L, h, 0.75, m, 1e-4, 0.8, seed=9 + model, interval=700, lo_hi=(lo, hi),
+                   prep_budget=pb)
         g.init()
         assert o.init() == 0
         g.run(max_rounds=30)

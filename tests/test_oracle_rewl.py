@@ -96,6 +96,21 @@ def test_caller_windows():
     assert max(errs) < 0.12, errs
 
 
+def test_prep_reaches_narrow_top_windows():
+    """Narrow windows at the top of the Ising range: the greedy walk from a random lattice
+    stalls below them; the restart from the checkerboard (k = N for even L) reaches them."""
+    L, B = 16, 256
+    lo, hi = [0, 200, 240, 250], [210, 245, 252, 256]
+    r = O.REWL(0, L, 4, 0.75, 3, 1e-3, 0.8, seed=8, interval=100, prep_budget=2, lo_hi=(lo, hi))
+    assert r.init() == 0
+    st = r.state()
+    for g in range(12):
+        w = g // 3
+        E = O.energy(0, L, st["spins"][g])
+        assert st["k"][g] == (E + 2 * L * L) // 4 and lo[w] <= st["k"][g] <= hi[w]
+    assert st["prep_restarts"][9:].sum() > 0  # the top window needed the restart
+
+
 def test_ising_8x8_config1_shape():
     ex = _exact(0, 8)
     fin = np.isfinite(ex)
