@@ -130,8 +130,7 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
     if (s.status != nullptr && s.status->done) return;
     int8_t *sp = reinterpret_cast<int8_t *>(base);
     long long *V = reinterpret_cast<long long *>(base + pad16(s.N));
-    float2 *stage = reinterpret_cast<float2 *>(V + padw(s.W));        // [32] (dk, ln u) of the batch
-    uint32_t *vis = reinterpret_cast<uint32_t *>(stage + 32);         // [W bits] bin visited
+    uint32_t *vis = reinterpret_cast<uint32_t *>(V + padw(s.W));      // [W bits] bin visited
     uint16_t *stamp = reinterpret_cast<uint16_t *>(vis + visw(s.W));  // [N] batch claims
 
     const int w = slot / s.m;
@@ -167,17 +166,15 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         mx = fmax(mx, fabs(x));
         V[b] = bad ? 0LL : __double2ll_rn(__dmul_rn(x, 0x1p32));
     }
-    // visited bits: bins any walker of the window visited before this launch, plus the ones
-    // this walker visits now (set with every visit below)
+    // visited bits: the bins any walker of the window had visited when this launch started,
+    // the start bin, and every bin this walker enters for the first time (always through the
+    // float64 path below)
     // (replay has no window mask: every bin counts as visited there)
     const uint8_t *gmask = s.mask ? s.mask + (size_t)w * s.W : nullptr;
-    for (int i = lane; i < visw(s.W); i += 32) {
-        uint32_t bits = 0u;
-        for (int j = 0; j < 32; ++j) {
-            const int b = 32 * i + j;
-            if (b < nb && (gmask == nullptr || gmask[b])) bits |= 1u << j;
-        }
-        vis[i] = bits;
+    for (int i = 0; i < visw(s.W); ++i) { // word i: bins 32i .. 32i+31, one per lane
+        const int b = 32 * i + lane;
+        const unsigned bits = __ballot_sync(FULL, b < nb && (gmask == nullptr || gmask[b]));
+        if (lane == 0) vis[i] = bits;
     }
     __syncwarp();
     if (lane == 0) vis[(k - lo) >> 5] |= 1u << ((k - lo) & 31); // the start bin
@@ -212,10 +209,9 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
             Lw = __fmaf_rn(__uint2float_rn((uint32_t)x), 0x1p-32f, (float)(int)(x >> 32));
         }
         // largest |Lw| of the cache (non-negative floats order like their bit patterns)
-        // Bins never visited (in the window before this launch, or by this walker now) keep
-        // their initial ln g while the others grow, so their cache values can be far off: they
-        // are marked NaN (a step there is flagged unsure and decided from the float64 values)
-        // and do not widen the float32 margin of every other step.
+        // Bins never visited keep their initial ln g while the others grow, so their cache
+        // values can be far off: they are marked NaN (a step there is flagged unsure and
+        // decided from the float64 values) and do not widen every other step's margin.
         const bool far = bin_ok && !((vis[(bj - lo) >> 5] >> ((bj - lo) & 31)) & 1u);
         const float Mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(bin_ok && !far ? fabsf(Lw) : 0.0f))) +
                          33.0f * lnf_f + 0x1p-20f;
@@ -249,7 +245,6 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         int snew;
         const int dk = propose_dk<ISING>(sp, lat, s.q, site, pr, snew);
         const float thr = lnu32(w2);
-        stage[lane] = make_float2(__int_as_float(dk), thr);
         // conflict-free prefix: proposal j may be resolved on the batch-start lattice only if
         // no earlier proposal of the batch sits on its site or a neighbour
         // claim stamp = (batch mod 2047) << 5 | lane, written by the lowest lane proposing the site;
@@ -282,14 +277,12 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         int myx = 16; // lane j: cache offset of the bin after step j
         float Lk = 0.0f;
         unsigned accbits = 0u, badbits = 0u, saccbits = 0u, srejbits = 0u;
-        const float4 *stage4 = reinterpret_cast<const float4 *>(stage);
 #pragma unroll
         for (int p = 0; p < 16; ++p) {
             const int i = 2 * p;
             if ((p & 3) == 0 && p > 0 && (badbits != 0u || i >= J)) break;
-            const float4 q = stage4[p]; // (dk, ln u) of steps i and i+1, a broadcast read
-            const int dk0 = __float_as_int(q.x), dk1 = __float_as_int(q.z);
-            const float th0 = q.y, th1 = q.w;
+            const int dk0 = __shfl_sync(FULL, dk, i), dk1 = __shfl_sync(FULL, dk, i + 1);
+            const float th0 = __shfl_sync(FULL, thr, i), th1 = __shfl_sync(FULL, thr, i + 1);
             const int x0 = xk + dk0;       // k' of step i
             const int xA = x0 + dk1;       // k' of step i+1 if step i moved
             const int xR = xk + dk1;       // k' of step i+1 if step i stayed
@@ -303,21 +296,17 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
             const bool moved0 = a0 && !dz0;
             const bool un0 = !dz0 && (CHECK ? !(L0 == INFINITY) : !(fabsf(e0) > M));
             const bool bad0 = (unsigned)x0 >= 32u || un0;
-            // step i+1, evaluated in both worlds (step i moved / stayed) alongside step i; the
-            // outcome of step i only selects, so the dependency chain per pair is one lookup,
-            // one decision and the selects
+            // step i+1 in the world the first step chose
             const float LA = (dk1 == -dk0) ? Lk : LA_; // back to the bin just left
             const float Lm = L0 + lnf_f;               // value after step i if moved
             const float Ls = Lk + lnf_f;               // value after step i if stayed
-            const bool dz1 = dk1 == 0;
-            const float eA = (Lm - LA) - th1, eR = (Ls - LR) - th1;
-            const bool aA = dz1 || eA > M, aR = dz1 || eR > M;
             const float Lc1 = moved0 ? Lm : Ls;
             const float L1 = moved0 ? LA : LR;
             const int x1 = moved0 ? xA : xR;
             const int xc1 = moved0 ? x0 : xk;
-            const float e1 = moved0 ? eA : eR;
-            const bool a1 = moved0 ? aA : aR;
+            const bool dz1 = dk1 == 0;
+            const float e1 = (Lc1 - L1) - th1;
+            const bool a1 = dz1 || e1 > M;
             const bool moved1 = a1 && !dz1;
             const bool un1 = !dz1 && (CHECK ? !(L1 == INFINITY) : !(fabsf(e1) > M));
             const bool bad1 = (unsigned)x1 >= 32u || un1;
@@ -352,19 +341,6 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         if (mine && !frozen)
             atomicAdd(reinterpret_cast<unsigned long long *>(&V[mypos - lo]),
                       (unsigned long long)lnfq);
-        {   // bins visited by the steps done: one warp OR of cache offsets, one lane writes
-            const uint32_t vm = __reduce_or_sync(FULL, mine ? 1u << myx : 0u);
-            if (lane == 0 && vm) {
-                const int off = k0 - 16 - lo; // bin of cache offset 0, window-local (>= -16)
-                if (off >= 0) {
-                    const unsigned long long v = (unsigned long long)vm << (off & 31);
-                    vis[off >> 5] |= (uint32_t)v;
-                    if (v >> 32) vis[(off >> 5) + 1] |= (uint32_t)(v >> 32);
-                } else {
-                    vis[0] |= vm >> (-off); // offsets below the window are never visited
-                }
-            }
-        }
         if (REPLAY && mine) {
             c.acc_out[(size_t)slot * T + t + lane] = (accbits >> lane) & 1u;
             c.dk_out[(size_t)slot * T + t + lane] = dk;
@@ -394,6 +370,8 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
                 ++nacc;
             }
             if (!frozen && lane == 0) V[k - lo] += lnfq;
+            // a bin reached for the first time is only ever entered here (its cache value is
+            // NaN until marked), so marking it here keeps the visited set complete
             if (lane == 0) vis[(k - lo) >> 5] |= 1u << ((k - lo) & 31);
             if (REPLAY && lane == 0) {
                 c.acc_out[(size_t)slot * T + t] = acc ? 1 : 0;

@@ -63,10 +63,10 @@ __host__ __device__ inline int visw(int W) { return (((W + 31) >> 5) + 3) & ~3; 
 
 // Shared memory of one walker in the move kernel: lattice (16-byte padded), int64 ln g
 // shadow over the window (padded to 4 bins; the visit counts are recovered from it), the
-// batch's (dk, ln u) staging (32 x 8 bytes), the visited-bin bit set, uint16 claim stamps.
+// visited-bin bit set, uint16 claim stamps per site.
 __host__ __device__ inline size_t move_smem_per_walker(int N, int W)
 {
-    return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 8u + 256u + (size_t)visw(W) * 4u +
+    return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 8u + (size_t)visw(W) * 4u +
            (size_t)((N + 7) & ~7) * 2u;
 }
 cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st);

@@ -158,7 +158,8 @@ def test_production_gives_g_em_6x6(R):
     assert fo.sum() >= 0.9 * fin.sum()
     # weight the error by how likely the point is at its energy
     ex = np.where(fin, np.exp(lex - lex.max()), 0)
-    pm = ex / ex.sum(axis=1, keepdims=True)
+    rs = ex.sum(axis=1, keepdims=True)
+    pm = np.divide(ex, rs, out=np.zeros_like(ex), where=rs > 0)
     sel = fo & (pm > 1e-2)
     d = np.abs(out[sel] - lex[sel])
     assert d.max() < 0.6 and d.mean() < 0.15, (d.max(), d.mean())
