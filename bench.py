@@ -168,6 +168,19 @@ def whole_job_rate(per_rank_units, world, rank_ms):
 
 
 # ----------------------------------------------------------------------------- main arms
+def workload_config(args, wl, world):
+    """The `config` object of a single-lattice workload (both arms print the same one)."""
+    per_round = wl["windows"] * wl["walkers"] * wl["interval"]
+    return {"workload": args.workload,
+            "model": "ising" if wl["model"] == 0 else f"potts{wl['model']}",
+            "L": wl["L"], "windows": wl["windows"], "walkers_per_window": wl["walkers"],
+            "walkers": wl["windows"] * wl["walkers"], "interval": wl["interval"],
+            "overlap": wl["overlap"], "flatness": wl["flatness"], "lnf_final": wl["lnf_final"],
+            "lnf_init": args.lnf_init, "attempts_per_step": per_round * world,
+            "parallelism": f"replicas{world}" if world > 1 else "1gpu",
+            "l2": "flushed (256 MB write) before every timed step"}
+
+
 KERNEL_SOURCES = ["paper_1402_2328_gb300/csrc/rewl_kernels.cu",
                   "paper_1402_2328_gb300/csrc/rewl_kernels.cuh",
                   "paper_1402_2328_gb300/csrc/rewl_device.cuh"]
@@ -648,31 +661,13 @@ def run_gpu(args, wl, rank, world):
     t_max, e2e_s = max_over_ranks([step_ms, e2e_s], device="cuda")
     attempts = per_round * args.steps * world
     value = whole_job_rate(per_round * args.steps, world, t_max)
-    # roofline of the move kernel (ALU/issue bound)
-    peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tinst = sms * 128 * sm_max_mhz * 1e6 / 1e12
-    move_avg_s = (move_ms / max(move_launches, 1)) / 1e3
-    achieved = ALG_INSTR_PER_ATTEMPT * per_round / move_avg_s / 1e12
     clocks = clk.summary()
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
-        "config": {"workload": args.workload, "model": "ising" if wl["model"] == 0 else f"potts{wl['model']}",
-                   "L": wl["L"], "windows": wl["windows"], "walkers_per_window": wl["walkers"],
-                   "walkers": r.nw, "interval": wl["interval"], "overlap": wl["overlap"],
-                   "flatness": wl["flatness"], "lnf_final": wl["lnf_final"],
-                   "lnf_init": args.lnf_init,
-                   "attempts_per_step": per_round * world,
-                   "parallelism": f"replicas{world}" if world > 1 else "1gpu",
-                   "l2": "flushed (256 MB write) before every timed step"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
-                     "frac": achieved / peak_tinst, "traffic": None,
-                     "kernel": "k_move", "kernel_ms_avg": move_avg_s * 1e3,
-                     "kernel_share_of_step": move_ms / step_ms if step_ms else None,
-                     "alg_inst_per_attempt": ALG_INSTR_PER_ATTEMPT,
-                     "peak_basis": f"{sms} SMs x 128 lanes x {sm_max_mhz:.0f} MHz (max SM clock)"},
+        "config": workload_config(args, wl, world),
+        "roofline": _roofline(per_round, move_ms, move_launches, sms, step_ms, args.workload),
         "e2e": {"value": attempts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": lng_bytes + 48,
                 "call": "rewl_run(1 round) + rewl_get_state(lng_mean) per step"},
@@ -757,8 +752,7 @@ def main():
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": tmax * 1e3 / rounds, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
-               "config": {"workload": args.workload, "L": wl["L"], "windows": wl["windows"],
-                          "walkers_per_window": wl["walkers"], "interval": wl["interval"]},
+               "config": workload_config(args, wl, world),
                "cpu_baseline": {"value": val, "unit": UNIT, "cores": procs, "kind": "oracle",
                                 "sample": f"{procs} independent oracle instances of the workload, "
                                           f"{rounds} rounds each ({attempts:.3g} attempts)"},

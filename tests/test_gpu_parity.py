@@ -344,3 +344,19 @@ def test_edge_cases():
     with pytest.raises(R.REWLError):
         g.set_param("no_such_key", 1)
     g.close()
+    with pytest.raises(R.REWLError):
+        R.REWL(0, 256, 64, 0.75, 1, 1e-3, 0.8)  # lattices up to L = 255
+    with pytest.raises(R.REWLError):
+        R.REWL(0, 255, 2, 0.75, 1, 1e-3, 0.8)  # window too wide for shared memory
+
+
+@pytest.mark.parametrize("model,L,h,m", [(0, 2, 1, 2), (3, 2, 2, 1), (0, 255, 64, 1)])
+def test_smallest_and_largest_lattices_bit_exact(model, L, h, m):
+    """L = 2 (4 sites) and L = 255 (65,025 sites, 226 KB of shared memory per walker)."""
+    g, o = _pair(model, L, h, m, lnf_final=1e-3, seed=17, interval=200)
+    g.init()
+    assert o.init() == 0
+    g.run(max_rounds=3)
+    o.run(3)
+    _same(g.state(), o.state())
+    g.close()
