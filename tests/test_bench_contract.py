@@ -1,0 +1,38 @@
+"""The benchmark's JSON contract on the CPU: the reference arm (the oracle on the host cores)
+prints one line with the keys the GPU arm prints, on the same workload config."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload",
+                          "ising_L8_h4_m1", "--steps", "2", "--warmup", "3"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = [x for x in out.stdout.splitlines() if x.startswith("{")][-1]
+    d = json.loads(line)
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    c = d["config"]
+    assert c["workload"] == "ising_L8_h4_m1" and c["L"] == 8 and c["windows"] == 4
+    assert c["attempts_per_step"] == 4 * 1 * 10_000
+
+
+def test_workload_config_matches_between_arms():
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    args = argparse.Namespace(workload="ising_L64_h32_m16", lnf_init=1.0)
+    c = bench.workload_config(args, bench.WORKLOADS["ising_L64_h32_m16"], 1)
+    assert c["walkers"] == 512 and c["attempts_per_step"] == 5_120_000
+    assert c["parallelism"] == "1gpu"
+    assert bench.workload_config(args, bench.WORKLOADS["ising_L64_h32_m16"], 4)["parallelism"] == "replicas4"

@@ -205,6 +205,26 @@ def test_config1_to_completion_bit_exact_and_accuracy():
     g.close()
 
 
+def test_potts_q3_3x3_against_enumeration():
+    """The small Potts check of the q = 10 workload: q = 3 on 3x3 (3^9 states enumerated),
+    two windows x four walkers, ln f to 1e-6, three seeds; each run equals the oracle's."""
+    ex = X.normalise_lng(np.array(X.exact_lng(3, 3, 3)), 9 * math.log(3))
+    fin = np.isfinite(ex)
+    errs = []
+    for seed in range(3):
+        g, o = _pair(3, 3, 2, 4, lnf_final=1e-6, seed=900 + seed, interval=500)
+        assert g.run() == "done"
+        o.init()
+        o.run(10 ** 7)
+        _same(g.state(), o.state())
+        out, _ = g.stitch(0)
+        assert np.array_equal(np.isfinite(out), fin)
+        errs.append(np.max(np.abs(out[fin] - ex[fin])))
+        g.close()
+    print(f"Potts q=3 3x3: max |d ln g| vs enumeration per seed = {np.round(errs, 4)}")
+    assert max(errs) < 0.25
+
+
 @pytest.mark.parametrize("model,L,h,m,rounds", [(0, 64, 32, 16, 2), (10, 40, 64, 16, 2)])
 def test_full_size_rounds_bit_exact(model, L, h, m, rounds):
     """The workloads of the benchmark, in the benchmark's launch configuration."""
