@@ -448,8 +448,13 @@ def run_warm(args):
         return out, lng
 
     results, lngs = {}, {}
-    for kind in args.warm_variants.split(","):
-        results[kind], lngs[kind] = target(seed_for(5, 1), kind)
+    per_seed = {}
+    for si in range(args.warm_seeds):
+        for kind in args.warm_variants.split(","):
+            res, lng = target(seed_for(5, 1 + si), kind)
+            per_seed.setdefault(kind, []).append((res, lng))
+    for kind, lst in per_seed.items():
+        results[kind], lngs[kind] = lst[0]
     cold = results.get("cold")
     warm = results.get("warm")
     for v, res in results.items():
@@ -467,6 +472,28 @@ def run_warm(args):
                            - args.warm_L ** 2 * math.log(2))
             res["max_abs_dlng_vs_exact"] = float(np.max(np.abs(lngs[v][f2] - ex_a[f2])))
     lng_cold, lng_warm = lngs.get("cold"), lngs.get("warm")
+
+    # mean over seeds: seconds, rounds, error against the exact result where it exists
+    ex_all = exact_lng_golden(args.warm_model, args.warm_L)
+    summary = {}
+    for kind, lst in per_seed.items():
+        secs = [r_["seconds"] for r_, _ in lst if r_["status"] == "done"]
+        errs = []
+        if ex_all is not None:
+            ex_a = np.array(ex_all)
+            f2 = np.isfinite(ex_a)
+            ex_a = ex_a - (ex_a[f2].max() + math.log(np.exp(ex_a[f2] - ex_a[f2].max()).sum())
+                           - args.warm_L ** 2 * math.log(2))
+            errs = [float(np.max(np.abs(l_[f2] - ex_a[f2]))) for _, l_ in lst if l_ is not None]
+        summary[kind] = {"seeds": len(lst), "done": len(secs),
+                         "seconds": [r_["seconds"] for r_, _ in lst],
+                         "mean_seconds": float(np.mean(secs)) if secs else None,
+                         "max_abs_dlng_vs_exact": errs,
+                         "mean_max_abs_dlng_vs_exact": float(np.mean(errs)) if errs else None}
+    if "cold" in summary and summary["cold"]["mean_seconds"]:
+        for kind, v in summary.items():
+            if v["mean_seconds"]:
+                v["mean_time_vs_cold"] = v["mean_seconds"] / summary["cold"]["mean_seconds"]
 
     def maxdiff(a, b_):
         if a is None or b_ is None:
@@ -490,7 +517,8 @@ def run_warm(args):
         "training_runs": train_stats, "training_status": st,
         "training_runs_seconds": t_train_runs, "training_samples": int(X.shape[0]),
         "fit_seconds": t_fit, "fit_loss": hist[-1][1],
-        "runs": results, "learned_windows": {"lo": lw_lo.tolist(), "hi": lw_hi.tolist()},
+        "runs": results, "over_seeds": summary,
+        "learned_windows": {"lo": lw_lo.tolist(), "hi": lw_hi.tolist()},
         "speedup_time": (cold["seconds"] / warm["seconds"])
         if cold and warm and warm["status"] == "done" and cold["status"] == "done" else None,
         "max_abs_dlng_warm_vs_cold": maxdiff(lng_warm, lng_cold),
@@ -718,6 +746,7 @@ def main():
     ap.add_argument("--speedup-h", default="1,2,4,8,16,32")
     ap.add_argument("--speedup-seeds", type=int, default=8)
     ap.add_argument("--speedup-interval", type=int, default=10_000)
+    ap.add_argument("--warm-seeds", type=int, default=1, help="target runs per variant")
     ap.add_argument("--warm-variants", default="cold,warm",
                     help="comma list of cold | warm | cold_lw | warm_eq (lw: learned windows), "
                          "each optionally @ln_f0, e.g. warm_eq@0.01")

@@ -71,6 +71,7 @@ def lib():
         L.or_rewl_get_extra.argtypes = [P, P, P, P]
         L.or_stitch.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, C.c_double, C.c_int,
                                 C.c_int, C.c_double, P, P]
+        L.or_rewl_swap.argtypes = [P, C.c_int, C.c_longlong]
         L.or_ln.argtypes = [C.c_double]
         L.or_ln.restype = C.c_double
         L.or_rewl_measure_em.argtypes = [P, C.c_int]
@@ -244,6 +245,10 @@ class REWL:
         mean = th[:, fin].mean(axis=0)
         err[fin] = np.sqrt((m - 1) / m * ((th[:, fin] - mean) ** 2).sum(axis=0))
         return err
+
+    def swap(self, w: int, rd: int):
+        """Only the exchange of windows (w, w+1) as round rd performs it (Eq. 1)."""
+        self._lib.or_rewl_swap(self._h, int(w), int(rd))
 
     def measure_em(self, on: bool = True):
         """Count every walker's (bin, up spins) after the moves of each round (Ising)."""

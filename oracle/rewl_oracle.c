@@ -601,6 +601,12 @@ static void swap_pair(or_rewl *r, int w, long long rd)
     }
 }
 
+/* The exchange of one window pair alone (round number rd), for tests of the exchange logic. */
+void or_rewl_swap(or_rewl *r, int w, long long rd)
+{
+    if (w >= 0 && w + 1 < r->h) swap_pair(r, w, rd);
+}
+
 /* One round: interval moves for every walker, flatness/advance, swaps. */
 void or_rewl_round(or_rewl *r)
 {
