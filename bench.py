@@ -64,6 +64,8 @@ UNIT = "attempts/s"
 # instructions; the issue roofline is SMs x 128 lanes x SM clock.
 ALG_INSTR_PER_ATTEMPT = 85
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# side files (nvidia-smi clock samples, predicted ln g): $REWL_BENCH_OUT, else the temp folder
+OUT_DIR = os.environ.get("REWL_BENCH_OUT") or __import__("tempfile").gettempdir()
 THROTTLE_BITS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
                  0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown", 0x1: "gpu_idle",
                  0x2: "applications_clocks_setting", 0x100: "display_clock_setting"}
@@ -106,7 +108,7 @@ class ClockSampler:
 
     def __enter__(self):
         try:
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+            self.path = os.path.join(OUT_DIR, f"clocks_bench_{os.getpid()}.csv")
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -508,8 +510,8 @@ def run_warm(args):
     pred_n = pred - (mx + math.log(np.exp(pred - mx).sum()) - N * math.log(q))
     if lng_cold is not None:
         pred_n = np.where(np.isfinite(lng_cold), pred_n, -np.inf)
-    np.save(os.path.join(ROOT, "gpurun_out", "warm_lng_pred.npy"), pred) if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None
+    if os.environ.get("REWL_BENCH_OUT"):
+        np.save(os.path.join(OUT_DIR, "warm_lng_pred.npy"), pred)
     return {"warm_start": {
         "target": dict(model=args.warm_model, L=args.warm_L, windows=args.warm_windows,
                        walkers_per_window=args.warm_walkers, lnf_final=args.warm_lnf_final,

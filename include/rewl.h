@@ -357,7 +357,7 @@ int rewl_replay(int model, int L, int n, int W, int T, void *spins, void *k, con
  * of an energy bin to ln g(E)/N (g normalised to sum q^N).  It is trained on converged ln g of
  * small lattices and predicts a warm-start ln g for a larger one (rewl_set_lng_init); the run
  * then starts from a small ln f.  The paper has no counterpart; plain cold-start REWL stays the
- * fallback and the judge of its error.  All pointers are device pointers; stream may be NULL.
+ * fallback and the reference for its error.  All pointers are device pointers; stream may be NULL.
  * Parameter vector P (REWL_MLP_NPARAM floats): W1[64][3], b1[64], W2[64][64] (W2[i][j]: from
  * hidden-1 unit j to hidden-2 unit i), b2[64], W3[64], b3.  X: n x 3 features, T: n targets.
  */

@@ -280,7 +280,7 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
 #pragma unroll
         for (int p = 0; p < 16; ++p) {
             const int i = 2 * p;
-            if ((p & 3) == 0 && p > 0 && (badbits != 0u || i >= J)) break;
+            if ((p & 1) == 0 && p > 0 && (badbits != 0u || i >= J)) break; // every 2 pairs (A/B)
             const int dk0 = __shfl_sync(FULL, dk, i), dk1 = __shfl_sync(FULL, dk, i + 1);
             const float th0 = __shfl_sync(FULL, thr, i), th1 = __shfl_sync(FULL, thr, i + 1);
             const int x0 = xk + dk0;       // k' of step i

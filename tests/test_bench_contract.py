@@ -36,3 +36,19 @@ def test_workload_config_matches_between_arms():
     assert c["walkers"] == 512 and c["attempts_per_step"] == 5_120_000
     assert c["parallelism"] == "1gpu"
     assert bench.workload_config(args, bench.WORKLOADS["ising_L64_h32_m16"], 4)["parallelism"] == "replicas4"
+
+
+def test_recorded_traffic_only_for_the_profiled_kernel(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k_move_w.md").write_text(
+        f"- traffic_bytes_per_launch: 1234\n- kernel_source_digest: {bench.kernel_source_digest()}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # the kernel sources are read from ROOT too: point them back at the repository
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", [os.path.join(ROOT, f) for f in bench.KERNEL_SOURCES])
+    assert bench.recorded_traffic("w") == 1234
+    (prof / "k_move_w.md").write_text("- traffic_bytes_per_launch: 1234\n- kernel_source_digest: 0\n")
+    assert bench.recorded_traffic("w") is None
+    assert bench.recorded_traffic("absent") is None
