@@ -584,6 +584,9 @@ __device__ __forceinline__ void check_window(const State &s, const int w, const 
     for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(FULL, nv, o);
     if (lane == 0) nvis_w[wid] = nv;
     const bool tmode = s.mode[w] != 0;
+    __shared__ int notflat; // walkers of the window not (yet) flat
+    if (threadIdx.x == 0) notflat = 0;
+    __syncthreads();
     for (int i = wid; i < m && !tmode; i += nwarp) {
         const int g = w * m + i;
         if (s.flat[g]) continue;
@@ -591,32 +594,30 @@ __device__ __forceinline__ void check_window(const State &s, const int w, const 
         unsigned long long sum = 0;
         uint32_t mn = 0xffffffffu;
         int cnt = 0;
-        for (int b = lane; b < nb; b += 32)
+#pragma unroll 4
+        for (int b = lane; b < nb; b += 32) { // both loads unconditional: they overlap
+            const uint32_t v = H[b];
             if (mask[b]) {
-                const uint32_t v = H[b];
                 sum += v;
                 mn = min(mn, v);
                 ++cnt;
             }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             sum += __shfl_xor_sync(FULL, sum, o);
             mn = min(mn, __shfl_xor_sync(FULL, mn, o));
             cnt += __shfl_xor_sync(FULL, cnt, o);
         }
-        if (lane == 0 && cnt > 0 &&
-            __dmul_rn((double)mn, (double)cnt) >= __dmul_rn(flatness, (double)sum))
-            s.flat[g] = 1;
+        if (lane == 0) {
+            if (cnt > 0 && __dmul_rn((double)mn, (double)cnt) >= __dmul_rn(flatness, (double)sum))
+                s.flat[g] = 1;
+            else
+                atomicAdd(&notflat, 1);
+        }
     }
     __syncthreads();
-    __shared__ int all;
-    if (threadIdx.x == 0) {
-        int a = 1;
-        for (int i = 0; i < m && !tmode; ++i) a &= s.flat[w * m + i];
-        all = a; // 1/t mode: every check averages and sets ln f = 1/t
-    }
-    __syncthreads();
-    if (!all) return;
+    if (notflat != 0) return; // 1/t mode: every check averages and sets ln f = 1/t
     // ln f after this advance (every thread computes the same value)
     long long nvis = 0;
     for (int i = 0; i < nwarp; ++i) nvis += nvis_w[i];
@@ -675,13 +676,13 @@ cudaError_t launch_check_batch(const State *states, const int2 *tab, int n, cons
                                cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_check_batch<<<n, 256, 0, st>>>(states, tab, prm);
+    k_check_batch<<<n, 512, 0, st>>>(states, tab, prm);
     return cudaGetLastError();
 }
 
 cudaError_t launch_check(const State &s, double flatness, double lnf_final, cudaStream_t st)
 {
-    k_check<<<s.h, 256, 0, st>>>(s, flatness, lnf_final);
+    k_check<<<s.h, 512, 0, st>>>(s, flatness, lnf_final);
     return cudaGetLastError();
 }
 
@@ -692,27 +693,39 @@ cudaError_t launch_check(const State &s, double flatness, double lnf_final, cuda
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void swap_pair(const State &s, const int pair)
 {
+    // one warp per window pair: the permutation's random draws and the m exchange decisions
+    // are lane-parallel (each decision touches its own two walker slots); only the
+    // Fisher-Yates swaps themselves run in order
     if (s.status->done) return;
     const long long rd = s.status->round;
     const int w = 2 * pair + (int)(rd & 1);
-    if (w + 1 >= s.h || threadIdx.x != 0) return;
+    if (w + 1 >= s.h) return;
+    const int lane = threadIdx.x & 31;
     const int m = s.m, W = s.W;
     __shared__ int perm[MAX_M];
-    for (int i = 0; i < m; ++i) perm[i] = i;
+    __shared__ int draw[MAX_M];
     const uint32_t tag = (s.inst << 8) | TAG_SWAP;
-    for (int i = m - 1; i >= 1; --i) {
-        const u32x4 r = philox((uint32_t)i, (uint32_t)rd, (uint32_t)w, tag, s.key0, s.key1);
-        const int j = (int)mulhi(r.x, (uint32_t)(i + 1));
-        const int t = perm[i];
-        perm[i] = perm[j];
-        perm[j] = t;
+    for (int i = lane; i < m; i += 32) {
+        perm[i] = i;
+        if (i >= 1) {
+            const u32x4 r = philox((uint32_t)i, (uint32_t)rd, (uint32_t)w, tag, s.key0, s.key1);
+            draw[i] = (int)mulhi(r.x, (uint32_t)(i + 1));
+        }
     }
+    __syncwarp();
+    if (lane == 0)
+        for (int i = m - 1; i >= 1; --i) {
+            const int j = draw[i];
+            const int t = perm[i];
+            perm[i] = perm[j];
+            perm[j] = t;
+        }
+    __syncwarp();
     const int loA = s.lo[w], hiA = s.hi[w], loB = s.lo[w + 1], hiB = s.hi[w + 1];
-    unsigned long long att = 0, acc = 0;
-    for (int i = 0; i < m; ++i) {
+    unsigned acc = 0;
+    for (int i = lane; i < m; i += 32) {
         const int a = w * m + i, b = (w + 1) * m + perm[i];
         const int kx = s.k[a], ky = s.k[b];
-        ++att;
         if (kx < loB || kx > hiB || ky < loA || ky > hiA) continue;
         const double *ga = s.lng + (size_t)a * W, *gb = s.lng + (size_t)b * W;
         const double lnP = __dadd_rn(__dsub_rn(ga[kx - loA], ga[ky - loA]),
@@ -732,8 +745,11 @@ __device__ __forceinline__ void swap_pair(const State &s, const int pair)
             ++acc;
         }
     }
-    s.swap_att[w] += att;
-    s.swap_acc[w] += acc;
+    acc = __reduce_add_sync(FULL, acc);
+    if (lane == 0) {
+        s.swap_att[w] += (unsigned long long)m;
+        s.swap_acc[w] += acc;
+    }
 }
 
 __global__ void k_swap(State s) { swap_pair(s, blockIdx.x); }
