@@ -14,7 +14,7 @@
  *     and enqueues all work on the stream given by rewl_set_stream (default: the legacy
  *     default stream).  A handle is not thread safe.
  *   - Lattices: 2 <= L <= 255 and the move kernel's shared memory (3 bytes per site plus
- *     12 bytes per window bin) must fit one CTA.
+ *     about 8.1 bytes per window bin) must fit one CTA (227 KB).
  *   - Models: model = 0 is the 2D Ising model E = -sum_<ij> s_i s_j (J = 1, s = +-1);
  *     model = q >= 2 is the q-state Potts model E = -sum_<ij> delta(s_i, s_j).  L x L
  *     square lattice with periodic boundaries, N = L*L sites, spins stored as int8.
