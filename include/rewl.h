@@ -72,8 +72,8 @@ int rewl_create(rewl_t *out, int model, int L, int windows, double overlap,
  * stream, default 0), "graph_rounds" (rounds per CUDA-graph replay, default 32; 0 = no
  * graph), "walkers_per_block" (warps per CTA of the move kernel; 0 = automatic),
  * "check_all" (1 = decide every move with the float64 path as well and count
- * disagreements; diagnostic), "schedule" (0 = ln f halving, f -> sqrt f, Sec. 2; 1 = the "1/t
- * algorithm" the paper names as an alternative: after a halving, once ln f < 1/t with
+ * disagreements; diagnostic), "schedule" (0 = ln f halving, f -> sqrt f, Sec. 2; 1 = the 1/t
+ * schedule of Belardinelli and Pereyra, an alternative Sec. 2 allows: after a halving, once ln f < 1/t with
  * t = moves per walker / visited bins of the window, ln f = 1/t is recomputed at every check,
  * where the m walkers' ln g are averaged, without a flatness test), "profile" (1 = time
  * move-kernel launches with CUDA events,
@@ -191,7 +191,7 @@ int rewl_stitch(rewl_t r, double *out, int cap, int norm, int *joins);
 
 /*
  * rewl_jackknife -- statistical error of the joined ln g from the m walkers' fragments
- * (Sec. 3: "standard resampling techniques"): each walker's ln g just before its window's last
+ * (Sec. 3: resampling over the walkers): each walker's ln g just before its window's last
  * averaging is kept; for j = 1..m the windows' means without walker j are joined as in
  * rewl_stitch (same norm), and err[b] = sqrt((m-1)/m * sum_j (theta_j[b] - mean)^2), NaN where a
  * resample has no value.  Needs m >= 2 and every window finished.  err: host, cap >= B+1.

@@ -15,7 +15,7 @@
  *   Sec. 2, Fig. 1a:           h equal-size windows with overlap o.
  *   Sec. 2:                    m independent walkers per window, each with its
  *                              own g and H; window advances when all m are flat;
- *                              g averaged and redistributed.
+ *                              the walkers' g combined and handed back.
  *   Sec. 2, Eq. (1):           replica exchange acceptance
  *                              min[1, g_i(E_X) g_j(E_Y) / (g_i(E_Y) g_j(E_X))],
  *                              impossible when an energy is outside the other
