@@ -570,9 +570,11 @@ __device__ __forceinline__ void check_window(const State &s, const int w, const 
     const int m = s.m, W = s.W, nb = s.hi[w] - s.lo[w] + 1;
     uint8_t *mask = s.mask + (size_t)w * W;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        uint8_t v = mask[b];
-        for (int i = 0; i < m && !v; ++i) v = s.H[(size_t)(w * m + i) * W + b] > 0u;
-        mask[b] = v;
+        if (mask[b]) continue;
+        uint32_t any = 0u; // the m loads are independent, so they overlap
+#pragma unroll 8
+        for (int i = 0; i < m; ++i) any |= s.H[(size_t)(w * m + i) * W + b];
+        if (any) mask[b] = 1;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
