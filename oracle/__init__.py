@@ -227,24 +227,8 @@ class REWL:
     def jackknife(self, norm: int = 0):
         """Per-bin jackknife error of the joined ln g over the m walker fragments (Sec. 3)."""
         st = self.state()
-        m, W = self.m, self.W
-        thetas = []
-        for j in range(m):
-            lngw = np.zeros((self.h, W), np.float64)
-            for w in range(self.h):
-                nb = int(self.hi[w] - self.lo[w] + 1)
-                acc = np.zeros(nb)
-                for i in range(m):
-                    if i != j:
-                        acc = acc + st["frag"][w * m + i, :nb]
-                lngw[w, :nb] = acc / (m - 1)
-            thetas.append(stitch(self.model, self.L, self.lo, self.hi, lngw, st["mask"], norm)[0])
-        th = np.array(thetas)
-        fin = np.all(np.isfinite(th), axis=0)
-        err = np.full(th.shape[1], np.nan)
-        mean = th[:, fin].mean(axis=0)
-        err[fin] = np.sqrt((m - 1) / m * ((th[:, fin] - mean) ** 2).sum(axis=0))
-        return err
+        return jackknife(self.model, self.L, self.lo, self.hi, st["frag"], st["mask"], self.m,
+                         norm)
 
     def swap(self, w: int, rd: int):
         """Only the exchange of windows (w, w+1) as round rd performs it (Eq. 1)."""
@@ -339,3 +323,31 @@ def join_em(lo, hi, S, B: int, N: int):
     if rc != 0:
         raise ValueError("oracle join_em: adjacent fragments share no point")
     return out, joins[: h - 1]
+
+
+def jackknife(model: int, L: int, lo, hi, frag, mask, m: int, norm: int = 0):
+    """Jackknife error of the joined ln g: frag [h*m][W] holds each walker's window-local ln g
+    (walker i of window w at row w*m+i); for j = 1..m the windows' means without walker j are
+    joined (Sec. 3, Eq. 2); err = sqrt((m-1)/m sum_j (theta_j - mean)^2), NaN where a
+    resample has no value."""
+    frag = np.asarray(frag, np.float64)
+    lo = np.asarray(lo)
+    hi = np.asarray(hi)
+    h, W = len(lo), frag.shape[1]
+    thetas = []
+    for j in range(m):
+        lngw = np.zeros((h, W), np.float64)
+        for w in range(h):
+            nb = int(hi[w] - lo[w] + 1)
+            acc = np.zeros(nb)
+            for i in range(m):
+                if i != j:
+                    acc = acc + frag[w * m + i, :nb]
+            lngw[w, :nb] = acc / (m - 1)
+        thetas.append(stitch(model, L, lo, hi, lngw, mask, norm)[0])
+    th = np.array(thetas)
+    fin = np.all(np.isfinite(th), axis=0)
+    err = np.full(th.shape[1], np.nan)
+    mean = th[:, fin].mean(axis=0)
+    err[fin] = np.sqrt((m - 1) / m * ((th[:, fin] - mean) ** 2).sum(axis=0))
+    return err

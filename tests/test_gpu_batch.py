@@ -128,4 +128,13 @@ def test_config4_batch_autotuned_equals_solo(R):
     assert info["instances"] == 24 and info["walkers"] == 6720
     for i in (0, 2, 3, 7, 12, 17, 23):
         _same(b.instance(i).state(), _solo(R, descs[i], 10_000, 5))
+    # the first instances of each model against the oracle, five rounds (the same rounds:
+    # the autotuner's trial rounds are ordinary rounds)
+    for i in (0, 3):
+        d = descs[i]
+        o = O.REWL(d["model"], d["L"], d["windows"], 0.75, d["walkers"], d["lnf_final"], 0.8,
+                   seed=d["seed"], instance=d["instance"], interval=10_000)
+        assert o.init() == 0
+        o.run(5)
+        _same(b.instance(i).state(), o.state())
     b.close()

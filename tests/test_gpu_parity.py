@@ -225,11 +225,12 @@ def test_potts_q3_3x3_against_enumeration():
     assert max(errs) < 0.25
 
 
-@pytest.mark.parametrize("model,L,h,m,rounds", [(0, 64, 32, 16, 2), (10, 40, 64, 16, 2)])
-def test_full_size_rounds_bit_exact(model, L, h, m, rounds):
-    """The workloads of the benchmark, in the benchmark's launch configuration."""
-    g, o = _pair(model, L, h, m, lnf_final=1e-8, seed=I.seed_for(2 if model == 0 else 3),
-                 interval=10_000)
+@pytest.mark.parametrize("model,L,h,m,rounds,cfg", [(0, 64, 32, 16, 2, 2), (10, 40, 64, 16, 2, 3),
+                                                   (10, 80, 64, 16, 2, 5)])
+def test_full_size_rounds_bit_exact(model, L, h, m, rounds, cfg):
+    """The workloads of the benchmark (Ising L = 64, Potts q = 10 L = 40 and L = 80), in the
+    benchmark's launch configuration."""
+    g, o = _pair(model, L, h, m, lnf_final=1e-8, seed=I.seed_for(cfg), interval=10_000)
     g.init()
     assert o.init() == 0
     g.run(max_rounds=rounds)

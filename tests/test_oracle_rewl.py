@@ -207,3 +207,55 @@ def test_stitch_picks_bin_where_derivatives_agree():
         valid[w, : len(ks)] = 1
     out, joins = O.stitch(0, 8, lo, hi, lngw, valid, norm=1)
     assert list(joins) == [k0]
+
+
+def _frag_setup(m=6, L=6, h=3):
+    """Exact 6x6 ln g cut into windows, one fragment row per walker."""
+    ex = _exact(0, L)
+    B = L * L
+    lo, hi = O.windows(B, h, 0.75)
+    W = int((hi - lo).max()) + 1
+    base = np.zeros((h * m, W))
+    mask = np.zeros((h, W), np.uint8)
+    for w in range(h):
+        nb = hi[w] - lo[w] + 1
+        seg = ex[lo[w]: hi[w] + 1]
+        mask[w, :nb] = np.isfinite(seg)
+        for i in range(m):
+            base[w * m + i, :nb] = np.where(np.isfinite(seg), seg, 0.0)
+    return ex, lo, hi, W, base, mask
+
+
+def test_jackknife_invariants():
+    """Identical fragments: zero error.  A constant offset per walker (a relative density of
+    states carries no absolute level): zero error.  Small perturbations: error linear in
+    their size."""
+    m = 6
+    ex, lo, hi, W, base, mask = _frag_setup(m)
+    fin = np.isfinite(ex)
+    assert np.nanmax(np.abs(O.jackknife(0, 6, lo, hi, base, mask, m))) < 1e-12
+    rng = np.random.default_rng(1)
+    off = base + rng.normal(0, 3, (base.shape[0], 1))
+    assert np.nanmax(np.abs(O.jackknife(0, 6, lo, hi, off, mask, m))) < 1e-10
+    z = rng.normal(0, 1, base.shape)
+    e1 = O.jackknife(0, 6, lo, hi, base + 1e-6 * z, mask, m)
+    e2 = O.jackknife(0, 6, lo, hi, base + 2e-6 * z, mask, m)
+    assert np.all(e1[fin] > 0)
+    np.testing.assert_allclose(e2[fin], 2 * e1[fin], rtol=1e-4)
+
+
+def test_jackknife_of_a_linear_statistic_is_the_standard_error():
+    """One window (nothing to join); only a bin of negligible weight varies between walkers,
+    so the joined ln g there is the plain walker mean, and the jackknife error must be the
+    textbook standard error of a mean, s / sqrt(m)."""
+    m, L = 8, 6
+    ex = _exact(0, L)
+    B = L * L
+    lo, hi = np.array([0]), np.array([B])
+    frag = np.tile(np.where(np.isfinite(ex), ex, 0.0), (m, 1))
+    mask = np.isfinite(ex).astype(np.uint8)[None, :]
+    b = 0  # the ground state: g = 2 out of 2^36
+    d = np.random.default_rng(4).normal(0, 1e-3, m)
+    frag[:, b] += d
+    err = O.jackknife(0, L, lo, hi, frag, mask, m)
+    assert err[b] == pytest.approx(np.std(d, ddof=1) / np.sqrt(m), rel=1e-6)
