@@ -344,16 +344,19 @@ def run_full(args, wl):
     import paper_1402_2328_gb300.rewl as R
 
     torch.cuda.set_device(0)
-    r = R.REWL(wl["model"], wl["L"], wl["windows"], wl["overlap"], wl["walkers"], wl["lnf_final"],
+    lnf_final = args.lnf_final if args.lnf_final else wl["lnf_final"]
+    r = R.REWL(wl["model"], wl["L"], wl["windows"], wl["overlap"], wl["walkers"], lnf_final,
                wl["flatness"], seed=seed_for(wl["config_id"]), interval=wl["interval"],
-               lnf_init=args.lnf_init)
+               lnf_init=args.lnf_init, schedule=args.schedule)
     t0 = time.perf_counter()
     r.init()
     t_init = time.perf_counter() - t0
     status = r.run(max_seconds=args.max_seconds)
     t_run = time.perf_counter() - t0 - t_init
     st = r.stats()
-    out = {"workload": args.workload, "status": status, "seconds_init": t_init,
+    out = {"workload": args.workload, "lnf_final": lnf_final,
+           "schedule": "1/t" if args.schedule else "halving", "status": status,
+           "seconds_init": t_init,
            "seconds_run": t_run, "rounds": st["rounds"], "attempts": st["attempts"],
            "attempts_per_s": st["attempts"] / max(t_run, 1e-9),
            "windows_finished": st["windows_finished"], "windows": r.h,
@@ -722,6 +725,10 @@ def main():
     ap.add_argument("--full-run", action="store_true",
                     help="run the workload to ln f < ln f_final and report the time to solution")
     ap.add_argument("--max-seconds", type=float, default=1800.0, help="cap of --full-run")
+    ap.add_argument("--lnf-final", type=float, default=0.0,
+                    help="--full-run: ln f_final instead of the workload's")
+    ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
+                    help="--full-run: 0 = ln f halving, 1 = switch to the 1/t schedule")
     ap.add_argument("--warm-start", action="store_true",
                     help="learned warm start experiment: train on small lattices, compare "
                          "warm vs cold on the target lattice")

@@ -279,6 +279,18 @@ def test_balanced_windows_pipeline():
     assert np.all(t1 > 0)
     lo, hi = pre.balanced_windows(8, 0.75)
     assert lo[0] == 0 and hi[-1] == 256 and np.all(lo[1:] <= hi[:-1])
+    # carried to a lattice by energy per site: the same lattice gives the same layout, a
+    # larger one a valid layout of its own bins that a run accepts
+    lo2, hi2 = pre.balanced_windows_for(16, 8, 0.75)
+    assert np.array_equal(lo2, lo) and np.array_equal(hi2, hi)
+    lo3, hi3 = pre.balanced_windows_for(32, 8, 0.75)
+    assert lo3[0] == 0 and hi3[-1] == 1024 and np.all(np.diff(lo3) > 0)
+    assert np.all(lo3[1:] <= hi3[:-1]) and np.all(np.diff(hi3) > 0)
+    big = R.REWL(0, 32, 8, 0.75, 1, 1e-3, 0.8, seed=7, interval=500)
+    big.set_windows(lo3, hi3)
+    big.init()
+    assert big.run(max_rounds=2) == "budget"
+    big.close()
     r = R.REWL(0, 16, 8, 0.75, 2, 1e-4, 0.8, seed=6, interval=2000)
     r.set_windows(lo, hi)
     assert r.run() == "done"
