@@ -78,11 +78,12 @@ static int walkers_per_block(const rewl_t r)
 {
     const size_t per = move_smem_per_walker(r->N, r->W);
     int g = r->wpb;
-    if (g <= 0) { // one warp per SM sub-partition first, then stack
+    if (g <= 0) { // one warp per SM sub-partition first; beyond 4 walkers per SM, more CTAs of
+                  // 4 (measured: 8 or 16 per CTA is slower than 4 for 1024 walkers)
         g = (r->nw + r->sms - 1) / r->sms;
         int p = 1;
         while (p < g) p <<= 1;
-        g = std::min(p, 16);
+        g = std::min(p, 4);
     }
     while (g > 1 && (size_t)g * per > MAX_SMEM_PER_CTA) g >>= 1;
     return g;
