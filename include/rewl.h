@@ -70,14 +70,15 @@ int rewl_create(rewl_t *out, int model, int L, int windows, double overlap,
  * exchange attempts, Sec. 2; default 10000), "prep_budget" (sweeps allowed to bring a
  * walker into its window, default 100), "instance" (0..2^24-1, enters the random
  * stream, default 0), "graph_rounds" (rounds per CUDA-graph replay, default 32; 0 = no
- * graph), "walkers_per_block" (warps per CTA of the move kernel; 0 = automatic),
- * "check_all" (1 = decide every move with the float64 path as well and count
- * disagreements; diagnostic), "schedule" (0 = ln f halving, f -> sqrt f, Sec. 2; 1 = the 1/t
- * schedule of Belardinelli and Pereyra, an alternative Sec. 2 allows: after a halving, once ln f < 1/t with
- * t = moves per walker / visited bins of the window, ln f = 1/t is recomputed at every check,
- * where the m walkers' ln g are averaged, without a flatness test), "profile" (1 = time
- * move-kernel launches with CUDA events,
- * see rewl_kernel_time; may be changed at any time).  Unknown key or bad value: INVALID_ARG.
+ * graph), "walkers_per_block" (warps per CTA of the move kernel; 0 = automatic: the power
+ * of two covering walkers / SMs, at most 4), "check_all" (1 = decide every move with the
+ * float64 path as well and count disagreements; diagnostic), "schedule" (0 = ln f halving,
+ * f -> sqrt f, Sec. 2; 1 = the 1/t schedule of Belardinelli and Pereyra, an alternative
+ * Sec. 2 allows: after a halving, once ln f < 1/t with t = moves per walker / visited bins
+ * of the window, ln f = 1/t is recomputed at every check, where the m walkers' ln g are
+ * averaged, without a flatness test), "profile" (1 = time move-kernel launches with CUDA
+ * events, see rewl_kernel_time; may be changed at any time).  Unknown key or bad value:
+ * INVALID_ARG.
  * Two keys may also be set after rewl_init (they drop the cached CUDA graph):
  * "production" (1 = rounds continue after every window finished: ln g and H stay frozen, the
  * walkers keep moving and exchanging, so every window performs a multicanonical walk with
