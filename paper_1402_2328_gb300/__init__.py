@@ -4,4 +4,4 @@ The hot path (WL moves, flatness test, window advance, replica exchange, joining
 in hand-written CUDA kernels behind the C ABI of include/rewl.h; ``rewl`` is its thin
 ctypes binding.
 """
-from .rewl import REWL, REWLError, lib, replay  # noqa: F401
+from .rewl import REWL, REWLBatch, REWLError, lib, replay  # noqa: F401
