@@ -808,6 +808,7 @@ def main():
                          f"{args.cpu_rounds} rounds each ({attempts:.3g} attempts, {tmax:.1f} s)"}
     if world > 1:
         import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))  # before NCCL binds a GPU
         torch.distributed.init_process_group("nccl")
     out = run_gpu_batch(args, wl, rank, world) if wl.get("batch") else run_gpu(args, wl, rank, world)
     if rank == 0:
