@@ -62,3 +62,17 @@ def test_oracle_is_not_imported_by_the_product():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
                 assert "rewl_oracle" not in src and "librewl_oracle" not in src, f
+
+
+def test_binding_argument_counts_match_header(built):
+    """Every prototype's parameter count equals the ctypes binding's argtypes length."""
+    import paper_1402_2328_gb300.rewl as R
+    lib = R.lib()
+    src = open(os.path.join(ROOT, "include", "rewl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = re.findall(r"\b(rewl_\w+)\s*\(([^)]*)\)\s*;", src)
+    assert len(protos) >= 55
+    for name, args in protos:
+        a = " ".join(args.split())
+        n = 0 if a in ("", "void") else a.count(",") + 1
+        assert len(getattr(lib, name).argtypes) == n, (name, n)
