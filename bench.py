@@ -196,24 +196,38 @@ def kernel_source_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes (read + write) per move launch from the committed ncu summary of this
-    workload, when it was captured from the current kernel source; else None."""
+RECORDED_KEYS = ("traffic_bytes_per_launch", "issue_slots_frac_of_sm_peak",
+                 "smem_wavefronts_frac_of_sm_peak", "kernel_source_digest")
+
+
+def recorded_profile(workload):
+    """Figures of the committed ncu summary of this workload's move kernel (DRAM bytes per
+    launch, issue-slot and shared-memory-wavefront fractions of the SM peaks), when it was
+    captured from the current kernel source; else {}."""
     path = os.path.join(ROOT, "profiles", f"k_move_{workload}.md")
     if not os.path.exists(path):
-        return None
+        return {}
     vals = {}
     for line in open(path):
         t = line.strip().lstrip("-* ").replace("`", "")
-        for key in ("traffic_bytes_per_launch", "kernel_source_digest"):
+        for key in RECORDED_KEYS:
             if t.startswith(key + ":"):
                 vals[key] = t.split(":", 1)[1].strip()
-    if vals.get("kernel_source_digest") != kernel_source_digest():
-        return None
-    try:
-        return int(float(vals["traffic_bytes_per_launch"]))
-    except (KeyError, ValueError):
-        return None
+    if vals.pop("kernel_source_digest", None) != kernel_source_digest():
+        return {}
+    out = {}
+    for key, v in vals.items():
+        try:
+            out[key] = float(v)
+        except ValueError:
+            pass
+    return out
+
+
+def recorded_traffic(workload):
+    """DRAM bytes (read + write) per move launch from the committed ncu summary, or None."""
+    v = recorded_profile(workload).get("traffic_bytes_per_launch")
+    return int(v) if v is not None else None
 
 
 def _roofline(per_launch_attempts, move_ms, move_launches, sms, step_ms, workload=None):
@@ -225,6 +239,8 @@ def _roofline(per_launch_attempts, move_ms, move_launches, sms, step_ms, workloa
     return {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
             "frac": achieved / peak_tinst,
             "traffic": recorded_traffic(workload) if workload else None, "kernel": "k_move",
+            "ncu": ({k: v for k, v in recorded_profile(workload).items()
+                     if k != "traffic_bytes_per_launch"} or None) if workload else None,
             "kernel_ms_avg": move_avg_s * 1e3,
             "kernel_share_of_step": move_ms / step_ms if step_ms else None,
             "alg_inst_per_attempt": ALG_INSTR_PER_ATTEMPT,
