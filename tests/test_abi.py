@@ -76,3 +76,14 @@ def test_binding_argument_counts_match_header(built):
         a = " ".join(args.split())
         n = 0 if a in ("", "void") else a.count(",") + 1
         assert len(getattr(lib, name).argtypes) == n, (name, n)
+
+
+def test_no_gpu_is_an_error_not_a_fallback(built):
+    """Without a usable CUDA device a handle cannot be created: the call fails with an error
+    (there is no CPU path behind the boundary)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import paper_1402_2328_gb300.rewl as R
+    with pytest.raises(R.REWLError):
+        R.REWL(0, 8, 2, 0.75, 1, 1e-3, 0.8)
