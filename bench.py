@@ -367,7 +367,8 @@ def run_full(args, wl):
     t0 = time.perf_counter()
     r.init()
     t_init = time.perf_counter() - t0
-    status = r.run(max_seconds=args.max_seconds)
+    with ClockSampler(0) as clk:
+        status = r.run(max_seconds=args.max_seconds)
     t_run = time.perf_counter() - t0 - t_init
     st = r.stats()
     out = {"workload": args.workload, "lnf_final": lnf_final,
@@ -378,7 +379,8 @@ def run_full(args, wl):
            "windows_finished": st["windows_finished"], "windows": r.h,
            "min_iteration": st["min_iteration"], "max_lnf": st["max_lnf"],
            "swap_acceptance": st["swap_accepted"] / max(st["swap_attempts"], 1),
-           "exact_fraction": st["exact_decisions"] / max(st["attempts"], 1)}
+           "exact_fraction": st["exact_decisions"] / max(st["attempts"], 1),
+           "clocks": clk.summary()}
     if status == "done":
         lng, joins = r.stitch(0)
         ex = exact_lng_golden(wl["model"], wl["L"])
