@@ -87,7 +87,8 @@ int rewl_create(rewl_t *out, int model, int L, int windows, double overlap,
  * zero an (E, M) histogram of h x W x (N+1) uint32 and, after the moves of every round, count
  * each walker's (bin, number of up spins) in its window; 0 = free it; INVALID_ARG when
  * h W (N+1) > 2^30 or (B+1)(N+1) > 2^28).  The histogram is not part of checkpoints.  Both
- * keys apply to handles made by rewl_create; batched instances (rewl_batch_*) ignore them.
+ * keys are meant for handles made by rewl_create: the batch runner (rewl_batch_*) does not
+ * run the (E, M) measurement.
  */
 int rewl_set_param(rewl_t r, const char *key, double value);
 
