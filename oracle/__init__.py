@@ -66,6 +66,8 @@ def lib():
         L.or_rewl_windows_get.argtypes = [P, P, P]
         L.or_rewl_get.argtypes = [P] * 17
         L.or_rewl_put.argtypes = [P] * 6
+        L.or_rewl_put_window.argtypes = [P] * 8
+        L.or_rewl_check.argtypes = [P, C.c_int]
         L.or_rewl_window_mean.argtypes = [P, C.c_int, P]
         L.or_rewl_set_schedule.argtypes = [P, C.c_int]
         L.or_rewl_get_extra.argtypes = [P, P, P, P]
@@ -218,6 +220,21 @@ class REWL:
                 for a, dt in ((spins, np.int8), (k, np.int32), (lng, np.float64),
                               (H, np.uint32), (step, np.uint64))]
         self._lib.or_rewl_put(self._h, *[(_p(a) if a is not None else None) for a in keep])
+
+    def put_window(self, lnf=None, iter=None, flat=None, finished=None, mask=None, mode=None,
+                   round=None):
+        """Overwrite window-level fields (lnf [h], iter [h], flat [nw], finished [h],
+        mask [h][W], mode [h]) and the round counter; None keeps a field."""
+        keep = [np.ascontiguousarray(a, dtype=dt) if a is not None else None
+                for a, dt in ((lnf, np.float64), (iter, np.int32), (flat, np.uint8),
+                              (finished, np.uint8), (mask, np.uint8), (mode, np.uint8))]
+        rd = C.c_longlong(int(round)) if round is not None else None
+        self._lib.or_rewl_put_window(self._h, *[(_p(a) if a is not None else None) for a in keep],
+                                     C.byref(rd) if rd is not None else None)
+
+    def check(self, w: int):
+        """Only the flatness test and window advance of window w (Sec. 2), as a round runs it."""
+        self._lib.or_rewl_check(self._h, int(w))
 
     def window_mean(self, w: int) -> np.ndarray:
         out = np.zeros(int(self.hi[w] - self.lo[w] + 1), dtype=np.float64)

@@ -705,6 +705,28 @@ void or_rewl_put(or_rewl *r, const int8_t *spins, const int *k, const double *ln
     if (step) memcpy(r->step, step, 8 * nw);
 }
 
+/* Test hook: overwrite the window-level state and the round counter (NULL: keep). */
+void or_rewl_put_window(or_rewl *r, const double *lnf, const int *iter, const uint8_t *flat,
+                        const uint8_t *finished, const uint8_t *mask, const uint8_t *mode,
+                        const long long *round)
+{
+    size_t h = (size_t)r->h;
+    if (lnf) memcpy(r->lnf, lnf, sizeof(double) * h);
+    if (iter) memcpy(r->iter, iter, sizeof(int) * h);
+    if (flat) memcpy(r->flat, flat, (size_t)r->nw);
+    if (finished) memcpy(r->finished, finished, h);
+    if (mask) memcpy(r->mask, mask, h * (size_t)r->W);
+    if (mode) memcpy(r->mode, mode, h);
+    if (round) r->round = *round;
+}
+
+/* Test hook: the flatness test and window advance of window w alone, as a round runs it
+ * (skipped for a finished window). */
+void or_rewl_check(or_rewl *r, int w)
+{
+    if (w >= 0 && w < r->h && !r->finished[w]) check_window(r, w);
+}
+
 /* Window average of ln g (O-8 formula, walker order) for window w. */
 void or_rewl_window_mean(const or_rewl *r, int w, double *out)
 {
