@@ -1,17 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the REWL hot path: Wang-Landau flip attempts per second.
 
-Workload (default): 2D Ising L=64, periodic, 32 windows at 75% overlap x 16 walkers per window
-(512 walkers), flatness 0.8, ln f from 1 halving towards 1e-8, 10^4 moves per walker between
-flatness checks / replica exchanges; lattices from a seeded uniform +-1 start.  One step is one
-round of the whole hot path: 10^4 WL moves per walker (+ ln g / H updates), the flatness test
-and window advance, and the replica exchange.
+Workload (default): 2D q=10 Potts L=80, periodic, 64 windows at 75% overlap x 16 walkers per
+window (1024 walkers), flatness 0.8, ln f from 1 halving towards 1e-8, 10^4 moves per walker
+between flatness checks / replica exchanges; lattices from seeded uniform states 0..9.  A round
+is one pass of the whole hot path: 10^4 WL moves per walker (+ ln g / H updates), the flatness
+test and window advance, the replica exchange and the end-of-round test; one step is
+--rounds-per-step rounds (default 128, about 0.1 s, so that the clock sampler sees the GPU
+under load).
 
-Timing: W untimed warm-up rounds, then K rounds, each bracketed by CUDA events on the stream
-the kernels run on, with the 129 MB L2 flushed (256 MB write) before every timed round.  The
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the stream
+the kernels run on, with the 129 MB L2 flushed (256 MB write) before every timed step.  The
 move kernel is additionally timed on its own (events inside the library) for the roofline.
-`e2e` repeats the K rounds through the blocking public call (rewl_run) and reads the window
-ln g back to the host every round.  The CPU baseline is the C oracle on the host cores.
+`e2e` repeats the K steps through the blocking public call (rewl_run) and reads the window
+ln g back to the host after every step.  The CPU baseline is the C oracle on the host cores.
 
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no collective on
 the data path); value = attempts of all ranks / max rank time.
@@ -178,7 +180,7 @@ def workload_config(args, wl, world):
             "L": wl["L"], "windows": wl["windows"], "walkers_per_window": wl["walkers"],
             "walkers": wl["windows"] * wl["walkers"], "interval": wl["interval"],
             "overlap": wl["overlap"], "flatness": wl["flatness"], "lnf_final": wl["lnf_final"],
-            "lnf_init": args.lnf_init, "attempts_per_step": per_round * world,
+            "lnf_init": args.lnf_init,
             "parallelism": f"replicas{world}" if world > 1 else "1gpu",
             "l2": "flushed (256 MB write) before every timed step"}
 
@@ -263,8 +265,10 @@ def run_gpu_batch(args, wl, rank, world):
     best, trial = b.autotune(rounds=1)  # 4 rounds of the simulation itself, untimed
     info = b.info()
     per_round = info["walkers"] * wl["interval"]
+    R = args.rounds_per_step
+    per_step = per_round * R
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    b.step(args.warmup)
+    b.step(args.warmup * R)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -276,7 +280,7 @@ def run_gpu_batch(args, wl, rank, world):
         for a, z in evs:
             flush.zero_()
             a.record(stream)
-            b.step(1)
+            b.step(R)
             z.record(stream)
         torch.cuda.synchronize()
     step_ms = sum(a.elapsed_time(z) for a, z in evs)
@@ -286,7 +290,7 @@ def run_gpu_batch(args, wl, rank, world):
     d2h = 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        b.run(max_rounds=1)
+        b.run(max_rounds=R)
         for i in range(len(descs)):
             x = b.instance(i).get_state("lng_mean")
             d2h += x.nbytes
@@ -299,35 +303,36 @@ def run_gpu_batch(args, wl, rank, world):
                    d["flatness"], seed=d["seed"], instance=d["instance"],
                    interval=wl["interval"], stream=stream)
         g.init()
-        g.step(args.warmup)
+        g.step(args.warmup * R)
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record(stream)
-        g.step(args.steps)
+        g.step(args.steps * R)
         z.record(stream)
         torch.cuda.synchronize()
         solo_ms += a.elapsed_time(z)
         g.close()
     t_max, e2e_s = max_over_ranks([step_ms, e2e_s], device="cuda")
-    attempts = per_round * args.steps * world
+    attempts = per_step * args.steps * world
     return {
-        "metric": METRIC, "value": whole_job_rate(per_round * args.steps, world, t_max), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": whole_job_rate(per_step * args.steps, world, t_max), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "instances": len(descs), "walkers": info["walkers"],
-                   "interval": wl["interval"], "attempts_per_step": per_round * world,
+                   "interval": wl["interval"],
                    "ctas_per_launch": info["ctas"], "autotuned_walkers_per_cta": best,
                    "autotune_ms_per_round": trial,
                    "parallelism": f"replicas{world}" if world > 1 else "1gpu",
                    "l2": "flushed (256 MB write) before every timed step"},
         "roofline": _roofline(per_round, move_ms, move_launches, sms, step_ms, args.workload),
-        "one_at_a_time": {"value": per_round * args.steps / (solo_ms / 1e3), "unit": UNIT,
+        "step_work": {"rounds": R, "attempts": per_step * world},
+        "one_at_a_time": {"value": per_step * args.steps / (solo_ms / 1e3), "unit": UNIT,
                           "ms_per_step": solo_ms / args.steps},
         "e2e": {"value": attempts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h // max(args.steps, 1),
-                "call": "rewl_batch_run(1 round) + rewl_get_state(lng_mean) of each instance"},
-        "gpu_launches": 4 * args.steps, "clocks": clk.summary(),
+                "call": f"rewl_batch_run({R} rounds) + rewl_get_state(lng_mean) of each instance"},
+        "gpu_launches": 4 * R * args.steps, "clocks": clk.summary(),
     }
 
 
@@ -675,9 +680,11 @@ def run_gpu(args, wl, rank, world):
                lnf_init=args.lnf_init)
     r.init()
     per_round = r.nw * wl["interval"]
+    R = args.rounds_per_step
+    per_step = per_round * R
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        r.step(1)
+        r.step(R)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -690,7 +697,7 @@ def run_gpu(args, wl, rank, world):
         for a, b in evs:
             flush.zero_()  # L2 flush, outside the timed events
             a.record(stream)
-            r.step(1)
+            r.step(R)
             b.record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -706,23 +713,24 @@ def run_gpu(args, wl, rank, world):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r.run(max_rounds=1)
+        r.run(max_rounds=R)
         _ = r.get_state("lng_mean")
     e2e_s = time.perf_counter() - t0
     t_max, e2e_s = max_over_ranks([step_ms, e2e_s], device="cuda")
-    attempts = per_round * args.steps * world
-    value = whole_job_rate(per_round * args.steps, world, t_max)
+    attempts = per_step * args.steps * world
+    value = whole_job_rate(per_step * args.steps, world, t_max)
     clocks = clk.summary()
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
         "config": workload_config(args, wl, world),
+        "step_work": {"rounds": R, "attempts": per_step * world},
         "roofline": _roofline(per_round, move_ms, move_launches, sms, step_ms, args.workload),
         "e2e": {"value": attempts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": lng_bytes + 48,
-                "call": "rewl_run(1 round) + rewl_get_state(lng_mean) per step"},
-        "gpu_launches": 4 * args.steps,
+                "call": f"rewl_run({R} rounds) + rewl_get_state(lng_mean) per step"},
+        "gpu_launches": 4 * R * args.steps,
         "clocks": clocks,
         "exact_fraction": st["exact_decisions"] / max(st["attempts"], 1),
     }
@@ -733,10 +741,12 @@ def run_gpu(args, wl, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ising_L64_h32_m16", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="potts10_L80_h64_m16", choices=sorted(WORKLOADS))
+    ap.add_argument("--rounds-per-step", type=int, default=128,
+                    help="rounds of the hot path in one timed step")
     ap.add_argument("--cpu-rounds", type=int, default=2, help="oracle rounds per core (baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lnf-init", type=float, default=1.0, help="ln f of the first iteration")
@@ -802,16 +812,22 @@ def main():
         # the oracle is the reference arm: rank 0 only, host cores only
         if rank != 0:
             return
+        # a step of this arm is one round of the workload on one core; the cores run
+        # `procs` independent instances in parallel, so the steps taken are procs x rounds and
+        # ms_per_step x steps equals the timed wall time
         rounds = max(1, math.ceil(args.steps / procs))
         val, tmax, attempts = oracle_throughput(wl, procs, rounds, warm=0)
+        steps = procs * rounds
         out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
-               "steps": args.steps, "warmup": args.warmup,
-               "ms_per_step": tmax * 1e3 / rounds, "higher_is_better": True, "scaling": "weak",
+               "steps": steps, "warmup": args.warmup,
+               "ms_per_step": tmax * 1e3 / steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
                "config": workload_config(args, wl, world),
+               "step_work": {"rounds": 1, "attempts": wl["windows"] * wl["walkers"] * wl["interval"]},
                "cpu_baseline": {"value": val, "unit": UNIT, "cores": procs, "kind": "oracle",
                                 "sample": f"{procs} independent oracle instances of the workload, "
-                                          f"{rounds} rounds each ({attempts:.3g} attempts)"},
+                                          f"{rounds} rounds each ({attempts:.3g} attempts, "
+                                          f"{tmax:.1f} s)"},
                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": 0}}
         print(json.dumps(out))

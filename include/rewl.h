@@ -59,15 +59,17 @@ typedef struct rewl_s *rewl_t;
  * hi_k = round((k+4)B/(h+3)), hi_{h-1} = B; other o use round(k s), round(k s + W) with
  * W = B/(1+(h-1)(1-o)), s = (1-o) W.  Adjacent windows must overlap, else INVALID_ARG.
  * Defaults: seed 0, ln f_init = 1, swap interval 10^4 moves, prep budget 100 sweeps.
- * *out receives the handle.  Allocates device memory on the current device.
+ * lnf_final < 2^-32 is refused (INVALID_ARG): the move kernel keeps ln g as an integer multiple
+ * of 2^-32 and could not add a smaller ln f.  *out receives the handle.  Allocates device memory on the current device.
  */
 int rewl_create(rewl_t *out, int model, int L, int windows, double overlap,
                 int walkers_per_window, double lnf_final, double flatness);
 
 /*
  * rewl_set_param -- before rewl_init.  Keys: "lnf_init" (ln f of the first iteration,
- * default 1), "interval" (WL moves per walker between two flatness checks and replica
- * exchange attempts, Sec. 2; default 10000), "prep_budget" (sweeps allowed to bring a
+ * default 1; 2^-32 <= lnf_init < 2^20), "interval" (WL moves per walker between two flatness
+ * checks and replica exchange attempts, Sec. 2; default 10000; at most 10^8), where
+ * interval * lnf_init must stay below 2^30 (the range of the move kernel's ln g shadow); "prep_budget" (sweeps allowed to bring a
  * walker into its window, default 100), "instance" (0..2^24-1, enters the random
  * stream, default 0), "graph_rounds" (rounds per CUDA-graph replay, default 32; 0 = no
  * graph), "walkers_per_block" (warps per CTA of the move kernel; 0 = automatic: the power
@@ -86,7 +88,7 @@ int rewl_create(rewl_t *out, int model, int L, int windows, double overlap,
  * max_seconds; 0 = back to the normal end test) and "measure_em" (Ising only; 1 = allocate and
  * zero an (E, M) histogram of h x W x (N+1) uint32 and, after the moves of every round, count
  * each walker's (bin, number of up spins) in its window; 0 = free it; INVALID_ARG when
- * h W (N+1) > 2^30 or (B+1)(N+1) > 2^28).  The histogram is not part of checkpoints.  Both
+ * h W (N+1) > 2^30 or (B+1)(N+1) > 2^28).  Both
  * keys are meant for handles made by rewl_create: the batch runner (rewl_batch_*) does not
  * run the (E, M) measurement.
  */
@@ -221,7 +223,10 @@ int rewl_dims(rewl_t r, int *out);
  *   "first_iter_round" int64[h] (rounds done when the window's first iteration ended, 0 if
  *   not yet: times `interval` it is the MC steps of Eq. (5)), "mode" uint8[h] (1: 1/t),
  *   "frag" float64[nw][W] (each walker's ln g just before its window's last averaging).
- * rewl_set_state accepts "spins", "k", "lng", "H", "step" (tests plant states with it).
+ * rewl_set_state accepts "spins", "k", "lng", "H", "step", "flat", "lnf" (each in [0, 2^20)),
+ * "iter", "finished" (the run's done flag is re-evaluated), "mask", "mode" (0/1 flags) and
+ * "round" (tests plant late-stage states with it); values outside those ranges are refused
+ * with REWL_ERR_INVALID_ARG.
  */
 int rewl_get_state(rewl_t r, const char *field, void *out, size_t bytes);
 int rewl_set_state(rewl_t r, const char *field, const void *in, size_t bytes);
@@ -244,9 +249,11 @@ int rewl_stats(rewl_t r, rewl_stats_t *out);
 
 /*
  * rewl_checkpoint / rewl_restore -- the whole state (lattices, bins, ln g, H, step
- * counters, flags, ln f, iterations, masks, round) to/from a binary file.  The random
- * stream is a function of the step counters, so a restored run continues bit for bit.
- * rewl_restore needs a handle created with the same parameters (else INVALID_ARG).
+ * counters, flags, ln f, iterations, masks, 1/t modes, saved fragments, round, the production
+ * switch and, when the (E, M) measurement is on, its histogram) to/from a binary file.  The
+ * random stream is a function of the step counters, so a restored run continues bit for bit.
+ * rewl_restore needs a handle created with the same parameters, including "schedule" (else
+ * INVALID_ARG); it takes over the checkpoint's production switch and (E, M) measurement.
  */
 int rewl_checkpoint(rewl_t r, const char *path);
 int rewl_restore(rewl_t r, const char *path);
@@ -347,8 +354,10 @@ const char *rewl_batch_last_error(rewl_batch_t b);
  *   lnf float64[n], frozen uint8[n] (1: no ln g/H update), words uint32[n][T][3]
  *   (w0 -> site, w1 -> Potts new state, w2 -> u = (w2 + 1/2) 2^-32),
  *   acc int32[n][T] and dk int32[n][T] (out: accepted flag and proposed bin change).
- * W >= max(hi-lo+1); a case with k outside [lo, hi], |ln g| >= 2^30 or ln f outside
- * (0, 2^20) makes the call fail with INVALID_ARG.  stream: cudaStream_t or NULL.
+ * W >= max(hi-lo+1); a case with k outside [lo, hi], |ln g| >= 2^30, or (not frozen) ln f
+ * outside [2^-32, 2^20) or max|ln g| + T ln f >= 2^30 (the range of the kernel's int64 ln g
+ * shadow) makes the call fail with INVALID_ARG and leaves that case's state untouched.
+ * stream: cudaStream_t or NULL.
  */
 int rewl_replay(int model, int L, int n, int W, int T, void *spins, void *k, const void *lo,
                 const void *hi, void *lng, void *H, const void *lnf, const void *frozen,
@@ -412,7 +421,8 @@ int rewl_thermo(const double *lng, int model, int L, const double *T, int nT, do
  * device (cudaGetSymbolAddress); make that first call before any stream capture.  Every call
  * zeroes the part of the array it uses and then overwrites it, so the array keeps the last
  * call's contents, and calls whose work overlaps on the GPU (other streams, other threads)
- * race on it: serialise them.
+ * race on it: serialise them.  The address is kept per device index for the life of the
+ * process, so no call may follow a cudaDeviceReset of that device.
  */
 #define REWL_REPLAY_STATIC_MAX_N 16384
 int rewl_replay_static(int model, int L, int n, int W, int T, void *spins, void *k,

@@ -187,7 +187,7 @@ int rewl_create(rewl_t *out, int model, int L, int windows, double overlap, int 
     }
     *out = nullptr;
     if (L < 2 || L > 255 || (model != 0 && (model < 2 || model > 127)) || windows < 1 ||
-        walkers_per_window < 1 || walkers_per_window > MAX_M || !(lnf_final > 0.0) ||
+        walkers_per_window < 1 || walkers_per_window > MAX_M || !(lnf_final >= 0x1p-32) ||
         !(flatness >= 0.0) || (long long)windows * walkers_per_window > (1LL << 24)) {
         g_err = "rewl_create: invalid argument";
         return REWL_ERR_INVALID_ARG;
@@ -261,8 +261,10 @@ int rewl_set_param(rewl_t r, const char *key, double v)
         return REWL_OK;
     }
     if (r->inited) return r->fail(REWL_ERR_STATE, "rewl_set_param after rewl_init");
-    if (k == "lnf_init" && v > 0.0 && std::isfinite(v)) r->lnf_init = v;
-    else if (k == "interval" && v >= 1 && v <= 1e8) r->interval = (long long)v;
+    // the move kernel's int64 ln g shadow needs 2^-32 <= ln f < 2^20 and interval * ln f < 2^30
+    if (k == "lnf_init" && v >= 0x1p-32 && v < 0x1p20 && v * (double)r->interval < 0x1p30) r->lnf_init = v;
+    else if (k == "interval" && v >= 1 && v <= 1e8 && std::floor(v) * r->lnf_init < 0x1p30)
+        r->interval = (long long)v;
     else if (k == "prep_budget" && v >= 1 && v <= 1e9) r->prep_budget = (long long)v;
     else if (k == "instance" && v >= 0 && v < 16777216.0) r->inst = (uint32_t)v;
     else if (k == "graph_rounds" && v >= 0 && v <= 4096) r->graph_rounds = (int)v;
@@ -768,17 +770,17 @@ static bool field(rewl_t r, const std::string &f, Field &out)
     else if (f == "H") out = {s.H, nw * W * 4, true};
     else if (f == "step") out = {s.step, nw * 8, true};
     else if (f == "acc") out = {s.acc, nw * 8, false};
-    else if (f == "flat") out = {s.flat, nw, false};
-    else if (f == "lnf") out = {s.lnf, h * 8, false};
-    else if (f == "iter") out = {s.iter, h * 4, false};
-    else if (f == "finished") out = {s.finished, h, false};
-    else if (f == "mask") out = {s.mask, h * W, false};
+    else if (f == "flat") out = {s.flat, nw, true};
+    else if (f == "lnf") out = {s.lnf, h * 8, true};
+    else if (f == "iter") out = {s.iter, h * 4, true};
+    else if (f == "finished") out = {s.finished, h, true};
+    else if (f == "mask") out = {s.mask, h * W, true};
     else if (f == "swap_att") out = {s.swap_att, h * 8, false};
     else if (f == "swap_acc") out = {s.swap_acc, h * 8, false};
     else if (f == "pstep") out = {s.pstep, nw * 8, false};
     else if (f == "prep_restarts") out = {s.restarts, nw * 4, false};
     else if (f == "first_iter_round") out = {s.it1_round, h * 8, false};
-    else if (f == "mode") out = {s.mode, h, false};
+    else if (f == "mode") out = {s.mode, h, true};
     else if (f == "frag") out = {s.frag, nw * W * 8, false};
     else if (f == "lo") out = {r->d_lohi, h * 4, false};
     else if (f == "hi") out = {r->d_lohi + h, h * 4, false};
@@ -851,10 +853,32 @@ int rewl_set_state(rewl_t r, const char *name, const void *in, size_t bytes)
         if (e != cudaSuccess) return r->cuda_fail(e, "set spins");
         return REWL_OK;
     }
+    if (f == "round") {
+        if (bytes != 8) return r->fail(REWL_ERR_BUFFER_TOO_SMALL, "round: bytes must be 8");
+        if (*(const long long *)in < 0) return r->fail(REWL_ERR_INVALID_ARG, "round: negative");
+        e = cudaMemcpyAsync(&r->st.status->round, in, 8, cudaMemcpyHostToDevice, r->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+        if (e != cudaSuccess) return r->cuda_fail(e, "rewl_set_state(round)");
+        return REWL_OK;
+    }
     Field fd;
     if (!field(r, f, fd) || !fd.writable) return r->fail(REWL_ERR_INVALID_ARG, "field not writable: " + f);
     if (bytes != fd.bytes) return r->fail(REWL_ERR_BUFFER_TOO_SMALL, f + ": bytes mismatch");
+    // values the kernels rely on
+    if (f == "flat" || f == "finished" || f == "mask" || f == "mode") {
+        for (size_t i = 0; i < bytes; ++i)
+            if (((const uint8_t *)in)[i] > 1) return r->fail(REWL_ERR_INVALID_ARG, f + ": values must be 0 or 1");
+    } else if (f == "lnf") {
+        for (size_t i = 0; i < bytes / 8; ++i) {
+            const double v = ((const double *)in)[i];
+            if (!(v >= 0.0 && v < 0x1p20)) return r->fail(REWL_ERR_INVALID_ARG, "lnf: values must lie in [0, 2^20)");
+        }
+    } else if (f == "iter") {
+        for (size_t i = 0; i < bytes / 4; ++i)
+            if (((const int *)in)[i] < 0) return r->fail(REWL_ERR_INVALID_ARG, "iter: negative");
+    }
     e = cudaMemcpyAsync(fd.dev, in, bytes, cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess && f == "finished") e = launch_set_done(r->st, r->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
     if (e != cudaSuccess) return r->cuda_fail(e, "rewl_set_state");
     return REWL_OK;
@@ -899,7 +923,7 @@ int rewl_stats(rewl_t r, rewl_stats_t *o)
 }
 
 // ---- checkpoints: header + the raw device arrays, in a fixed order
-static const char CKPT_MAGIC[8] = {'R', 'E', 'W', 'L', 'C', 'K', '0', '1'};
+static const char CKPT_MAGIC[8] = {'R', 'E', 'W', 'L', 'C', 'K', '0', '2'};
 struct CkptHeader {
     char magic[8];
     int model, L, h, m, W, N, spin_stride;
@@ -907,6 +931,9 @@ struct CkptHeader {
     double lnf_final, flatness;
     uint64_t seed;
     uint32_t inst;
+    int schedule;   // ln f schedule (must match the handle's)
+    int production; // production mode of the run (restored)
+    int has_hem;    // the (E, M) histogram follows the fields (restored)
 };
 
 static std::vector<Field> ckpt_fields(rewl_t r)
@@ -922,6 +949,8 @@ static std::vector<Field> ckpt_fields(rewl_t r)
             {s.it1_round, h * 8, true},         {s.mode, h, true}, {s.frag, nw * W * 8, true}};
 }
 
+static size_t hem_bytes(rewl_t r) { return (size_t)r->h * r->W * ((size_t)r->N + 1) * 4u; }
+
 int rewl_checkpoint(rewl_t r, const char *path)
 {
     if (!r || !path) return REWL_ERR_INVALID_ARG;
@@ -931,10 +960,13 @@ int rewl_checkpoint(rewl_t r, const char *path)
     hd.model = r->model; hd.L = r->L; hd.h = r->h; hd.m = r->m; hd.W = r->W; hd.N = r->N;
     hd.spin_stride = r->st.spin_stride; hd.interval = r->interval; hd.lnf_final = r->lnf_final;
     hd.flatness = r->flatness; hd.seed = r->seed; hd.inst = r->inst;
+    hd.schedule = r->schedule; hd.production = r->production; hd.has_hem = r->st.hem != nullptr;
+    std::vector<Field> fields = ckpt_fields(r);
+    if (r->st.hem) fields.push_back({r->st.hem, hem_bytes(r), true});
     FILE *fp = std::fopen(path, "wb");
     if (!fp) return r->fail(REWL_ERR_IO, std::string("cannot open ") + path);
     bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1;
-    for (const Field &f : ckpt_fields(r)) {
+    for (const Field &f : fields) {
         if (!ok) break;
         std::vector<unsigned char> buf(f.bytes);
         cudaError_t e = cudaMemcpyAsync(buf.data(), f.dev, f.bytes, cudaMemcpyDeviceToHost, r->stream);
@@ -963,12 +995,15 @@ int rewl_restore(rewl_t r, const char *path)
     if (hd.model != r->model || hd.L != r->L || hd.h != r->h || hd.m != r->m || hd.W != r->W ||
         hd.N != r->N || hd.spin_stride != r->st.spin_stride || hd.interval != r->interval ||
         hd.lnf_final != r->lnf_final || hd.flatness != r->flatness || hd.seed != r->seed ||
-        hd.inst != r->inst) {
+        hd.inst != r->inst || hd.schedule != r->schedule || (hd.production != 0 && hd.production != 1) ||
+        (hd.has_hem != 0 && hd.has_hem != 1) || (hd.has_hem && r->model != 0)) {
         std::fclose(fp);
         return r->fail(REWL_ERR_INVALID_ARG, "checkpoint parameters differ from the handle's");
     }
+    std::vector<Field> fields = ckpt_fields(r);
     std::vector<std::vector<unsigned char>> bufs;
-    for (const Field &f : ckpt_fields(r)) {
+    if (hd.has_hem) fields.push_back({nullptr, hem_bytes(r), true});
+    for (const Field &f : fields) {
         bufs.emplace_back(f.bytes);
         if (std::fread(bufs.back().data(), 1, f.bytes, fp) != f.bytes) {
             std::fclose(fp);
@@ -982,12 +1017,21 @@ int rewl_restore(rewl_t r, const char *path)
     for (int w = 0; w < r->h; ++w)
         if (lohi[w] != r->lo[w] || lohi[r->h + w] != r->hi[w])
             return r->fail(REWL_ERR_INVALID_ARG, "checkpoint window layout differs");
+    // run mode and (E, M) measurement as they were when the checkpoint was written
+    int rc = rewl_set_param(r, "measure_em", hd.has_hem ? 1.0 : 0.0);
+    if (rc != REWL_OK && !(rc == REWL_ERR_INVALID_ARG && !hd.has_hem)) return rc;
+    if (hd.has_hem) fields.back().dev = r->st.hem;
     size_t i = 0;
-    for (const Field &f : ckpt_fields(r)) {
+    for (const Field &f : fields) {
         cudaError_t e = cudaMemcpyAsync(f.dev, bufs[i++].data(), f.bytes, cudaMemcpyHostToDevice, r->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
         if (e != cudaSuccess) return r->cuda_fail(e, "restore");
     }
+    if (r->graph) cudaGraphExecDestroy(r->graph);
+    r->graph = nullptr;
+    r->production = hd.production;
+    r->st.production = hd.production;
+    r->st.schedule = r->schedule; // rewl_init, which a restore replaces, sets it otherwise
     r->inited = true;
     return REWL_OK;
 }
@@ -1054,9 +1098,13 @@ int rewl_replay(int model, int L, int n, int W, int T, void *spins, void *k, con
     s.hi = (const int *)hi;
     s.lnf = (double *)lnf;
     s.finished = (uint8_t *)frozen;
-    s.step = dmalloc<unsigned long long>((size_t)n, e);
-    s.acc = dmalloc<unsigned long long>((size_t)n, e);
-    s.status = dmalloc<DevStatus>(1, e);
+    // scratch: allocated here, zeroed on the caller's stream so the kernel is ordered after it
+    e = cudaMalloc(&s.step, (size_t)n * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&s.acc, (size_t)n * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&s.status, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.step, 0, (size_t)n * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.acc, 0, (size_t)n * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.status, 0, sizeof(DevStatus), st);
     if (e != cudaSuccess) {
         g_err = std::string("rewl_replay alloc: ") + cudaGetErrorString(e);
         cudaFree(s.step); cudaFree(s.acc); cudaFree(s.status);

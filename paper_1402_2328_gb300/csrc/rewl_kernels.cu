@@ -179,7 +179,10 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
     __syncwarp();
     if (lane == 0) vis[(k - lo) >> 5] |= 1u << ((k - lo) & 31); // the start bin
     mx = warp_max(mx);
-    if (__any_sync(FULL, bad) || !(lnf >= 0x1p-32 && lnf < 0x1p20)) {
+    // the shadow of a running window ends the launch below (max |ln g| + T ln f) 2^32 < 2^62,
+    // and ln f 2^32 must not round to zero; a frozen window adds nothing to it
+    const bool lnf_ok = frozen || (lnf >= 0x1p-32 && lnf < 0x1p20 && mx + (double)T * lnf < 0x1p30);
+    if (__any_sync(FULL, bad) || !lnf_ok) {
         // the int64 shadow would overflow or lose the increment: leave the state untouched
         if (lane == 0) atomicOr(&s.status->err, ERR_RANGE);
         return;

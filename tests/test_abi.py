@@ -87,3 +87,14 @@ def test_no_gpu_is_an_error_not_a_fallback(built):
     import paper_1402_2328_gb300.rewl as R
     with pytest.raises(R.REWLError):
         R.REWL(0, 8, 2, 0.75, 1, 1e-3, 0.8)
+
+
+def test_create_refuses_lnf_final_below_the_shadow_resolution(built):
+    """ln f_final < 2^-32 cannot be added to the move kernel's 2^-32 fixed-point ln g: refused
+    by the argument check, before any device call."""
+    import paper_1402_2328_gb300.rewl as R
+    lib = R.lib()
+    h = ctypes.c_void_p()
+    rc = lib.rewl_create(ctypes.byref(h), 0, 8, 2, 0.75, 1, 2.0 ** -33, 0.8)
+    assert rc == -1 and not h.value
+    assert b"invalid argument" in lib.rewl_last_error(None)

@@ -24,7 +24,14 @@ def test_reference_arm_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     c = d["config"]
     assert c["workload"] == "ising_L8_h4_m1" and c["L"] == 8 and c["windows"] == 4
-    assert c["attempts_per_step"] == 4 * 1 * 10_000
+    assert d["step_work"] == {"rounds": 1, "attempts": 4 * 1 * 10_000}
+    # a step is one round on one core; the cores run in parallel, so the steps reported are
+    # cores x rounds and ms_per_step x steps is the timed wall time of the sample
+    cores = d["cpu_baseline"]["cores"]
+    assert d["steps"] == cores * max(1, -(-2 // cores))
+    wall = float(d["cpu_baseline"]["sample"].rsplit(", ", 1)[1].split(" s")[0])
+    assert abs(d["ms_per_step"] * d["steps"] / 1e3 - wall) <= 0.05 + 0.01 * wall
+    assert abs(d["value"] - d["steps"] * 40_000 / (d["ms_per_step"] * d["steps"] / 1e3)) < 1e-6 * d["value"]
 
 
 def test_workload_config_matches_between_arms():
@@ -33,7 +40,7 @@ def test_workload_config_matches_between_arms():
     import bench
     args = argparse.Namespace(workload="ising_L64_h32_m16", lnf_init=1.0)
     c = bench.workload_config(args, bench.WORKLOADS["ising_L64_h32_m16"], 1)
-    assert c["walkers"] == 512 and c["attempts_per_step"] == 5_120_000
+    assert c["walkers"] == 512 and c["interval"] == 10_000
     assert c["parallelism"] == "1gpu"
     assert bench.workload_config(args, bench.WORKLOADS["ising_L64_h32_m16"], 4)["parallelism"] == "replicas4"
 
