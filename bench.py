@@ -6,7 +6,7 @@ window (1024 walkers), flatness 0.8, ln f from 1 halving towards 1e-8, 10^4 move
 between flatness checks / replica exchanges; lattices from seeded uniform states 0..9.  A round
 is one pass of the whole hot path: 10^4 WL moves per walker (+ ln g / H updates), the flatness
 test and window advance, the replica exchange and the end-of-round test; one step is
---rounds-per-step rounds (default 128, about 0.1 s, so that the clock sampler sees the GPU
+--rounds-per-step rounds (default 256, about 0.2 s, so that the clock sampler sees the GPU
 under load).
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the stream
@@ -745,7 +745,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="potts10_L80_h64_m16", choices=sorted(WORKLOADS))
-    ap.add_argument("--rounds-per-step", type=int, default=128,
+    ap.add_argument("--rounds-per-step", type=int, default=256,
                     help="rounds of the hot path in one timed step")
     ap.add_argument("--cpu-rounds", type=int, default=2, help="oracle rounds per core (baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

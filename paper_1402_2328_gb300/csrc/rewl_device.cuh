@@ -94,57 +94,56 @@ __device__ __forceinline__ float lnu32(uint32_t w)
     return __logf(u);
 }
 
-// x + f + f + ... (c additions in round-to-nearest float64), computed without the loop
-// when f is a power of two: inside one binade [2^e, 2^(e+1)) with f >= ulp(x) every
-// addition is exact, so only the additions that cross into the next binade can round;
-// those are done one at a time.  Non-positive x is walked to the first positive value the
-// same way (additions toward zero are exact).  Anything else takes the plain loop.
+// x + f + f + ... (c additions, each rounded to nearest even in float64), without the loop.
+// Inside one binade (x a multiple of the spacing u there) every sum x + f = x + a u + r, with
+// a = floor(f/u) and 0 <= r < u, rounds to x + a u (r < u/2) or x + (a+1) u (r > u/2)
+// whatever x is, so every addition that stays in the binade adds the same d and a run of them
+// is one exact fma.  The addition that may leave the binade, and ties (r = u/2, whose result
+// depends on the parity of x/u), are done one at a time; so are zero and tiny |x|.  For
+// x < 0 the sums run towards zero and the binade ends at -2^e.
 __device__ __forceinline__ double seqadd(double x, double f, uint32_t c)
 {
     if (c == 0u) return x;
-    const long long fb = __double_as_longlong(f);
-    const bool pow2 = f > 0.0 && (fb & 0x000fffffffffffffLL) == 0 && ((fb >> 52) & 0x7ff) != 0;
-    if (pow2) {
-        double cf = (double)c;
-        if (x < 0.0) {
-            const int exn = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
-            // additions toward zero are exact only while f >= ulp(x)
-            if (exn <= 52 || f < __longlong_as_double((long long)(exn - 52) << 52)) {
-                for (uint32_t i = 0; i < c; ++i) x = __dadd_rn(x, f);
-                return x;
-            }
-            // steps that keep x <= 0: floor(-x / f) (exact: f is a power of two)
-            const double nneg = floor(__ddiv_rn(-x, f));
-            if (cf <= nneg) return __fma_rn(cf, f, x); // exact, result <= 0
-            x = __fma_rn(nneg, f, x);                 // exact, in (-f, 0]
-            cf = __dsub_rn(cf, nneg);
-            x = __dadd_rn(x, f); // the step that crosses zero rounds like the loop does
-            cf = __dsub_rn(cf, 1.0);
-        }
-        while (cf > 0.0) {
-            if (x == 0.0) {
-                x = f;
-                cf = __dsub_rn(cf, 1.0);
-                continue;
-            }
-            const long long xb = __double_as_longlong(x);
-            const int ex = (int)((xb >> 52) & 0x7ff);
-            if (ex == 0) break; // subnormal: plain loop below
-            const double ulp = __longlong_as_double((long long)(ex > 52 ? ex - 52 : 1) << 52);
-            if (ex <= 52 || f < ulp) break; // f below ulp(x): plain loop below
-            const double next = __longlong_as_double((long long)(ex + 1) << 52);
-            // additions j with x + j f < next are exact: j <= ceil((next - x)/f) - 1
-            const double nsafe = ceil(__ddiv_rn(__dsub_rn(next, x), f)) - 1.0;
-            if (cf <= nsafe) return __fma_rn(cf, f, x);
-            x = __fma_rn(nsafe, f, x);
-            cf = __dsub_rn(cf, nsafe);
-            x = __dadd_rn(x, f); // crossing into the next binade: one correctly rounded add
-            cf = __dsub_rn(cf, 1.0);
-        }
-        for (; cf > 0.0; cf = __dsub_rn(cf, 1.0)) x = __dadd_rn(x, f);
+    if (!(f > 0.0) || !(f < INFINITY)) {
+        for (uint32_t i = 0; i < c; ++i) x = __dadd_rn(x, f);
         return x;
     }
-    for (uint32_t i = 0; i < c; ++i) x = __dadd_rn(x, f);
+    double cf = (double)c;
+    while (cf > 0.0) {
+        const long long xb = __double_as_longlong(x);
+        const int ex = (int)((xb >> 52) & 0x7ff);
+        double n = 0.0, d = 0.0;
+        if (ex > 53 && ex < 2046) {
+            const double u = __longlong_as_double((long long)(ex - 52) << 52);      // ulp(x)
+            const double inv_u = __longlong_as_double((long long)(2098 - ex) << 52); // 1 / u
+            // the sums stay on the grid of spacing u while they lie below 2^(e+1) (x > 0) or
+            // at or beyond -2^e (x < 0): D is the room left
+            const double top = __longlong_as_double((long long)(x > 0.0 ? ex + 1 : ex) << 52);
+            const double D = x > 0.0 ? __dsub_rn(top, x) : __dsub_rn(-x, top);
+            if (f <= D) {
+                const double a = floor(__dmul_rn(f, inv_u)); // f = a u + r, 0 <= r < u
+                const double r = __fma_rn(-a, u, f);
+                const double h = __dmul_rn(u, 0.5);
+                if (r != h) { // not a tie: every addition in the binade adds d
+                    d = __dmul_rn(r < h ? a : __dadd_rn(a, 1.0), u);
+                    if (d == 0.0) return x; // f < u/2: no addition changes x
+                    // additions j with (j+1) d + u/2 <= D stay in the binade
+                    const double X = __dsub_rn(D, h);
+                    if (X >= d) {
+                        n = floor(__ddiv_rn(X, d));
+                        if (__fma_rn(n, d, -X) > 0.0) n = __dsub_rn(n, 1.0);
+                    }
+                }
+            }
+        }
+        if (n > 0.0) {
+            if (cf <= n) return __fma_rn(cf, d, x); // exact: a multiple of u inside the binade
+            x = __fma_rn(n, d, x);
+            cf = __dsub_rn(cf, n);
+        }
+        x = __dadd_rn(x, f); // one addition that may leave the binade (or a tie)
+        cf = __dsub_rn(cf, 1.0);
+    }
     return x;
 }
 

@@ -247,15 +247,31 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         const int pr = ISING ? 0 : (int)mulhi(w1, (uint32_t)(s.q - 1));
         int snew;
         const int dk = propose_dk<ISING>(sp, lat, s.q, site, pr, snew);
-        const float thr = lnu32(w2);
+        // a proposal that keeps the energy is always accepted and keeps the bin: the serial
+        // walk sees it as a sure non-move (threshold +inf), the lane itself records the flip
+        const bool dz = dk == 0;
+        const float thr = dz ? INFINITY : lnu32(w2);
         // conflict-free prefix: proposal j may be resolved on the batch-start lattice only if
-        // no earlier proposal of the batch sits on its site or a neighbour
-        // claim stamp = (batch mod 2047) << 5 | lane, written by the lowest lane proposing the site;
-        // a stale stamp of an old batch with the same low bits can only cut a batch early
+        // no earlier proposal of the batch sits on its site or a neighbour.
+        // Claim stamp = (batch mod 2047) << 5 | lane of the lowest lane proposing the site: every
+        // lane writes its stamp, then a lane that finds a later lane's stamp on its site writes
+        // again until none does (at most one extra pass unless three lanes share a site).  A
+        // stale stamp of an old batch with the same low bits can only cut a batch early.
         const unsigned btag = batch % 2047u;
-        const unsigned peers = __match_any_sync(FULL, lane < n ? site : -1 - lane);
-        if (lane < n && lane == __ffs(peers) - 1) stamp[site] = (uint16_t)((btag << 5) | (unsigned)lane);
+        const uint16_t mystamp = (uint16_t)((btag << 5) | (unsigned)lane);
+        if (lane < n) stamp[site] = mystamp;
         __syncwarp();
+        for (int it = 0; it < 32; ++it) { // each pass lowers some stamp: ends within 32 passes
+            bool again = false;
+            if (lane < n) {
+                const unsigned v = stamp[site];
+                again = (v >> 5) == btag && (int)(v & 31u) > lane;
+            }
+            __syncwarp();
+            if (!__any_sync(FULL, again)) break;
+            if (again) stamp[site] = mystamp;
+            __syncwarp();
+        }
         bool conflict = false;
         {
             const int xs[5] = {site, nl, nr, nu, nd};
@@ -269,86 +285,107 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         const int J = cmask ? (__ffs(cmask) - 1) : n; // >= 1: lane 0 never conflicts
 
         // ---- serial phase: the path k_0, k_1, ... only.  Every step runs unconditionally;
-        // a step that is too close to call in float32 or whose k' leaves the cache is only
-        // flagged, and the batch is cut at the first flagged step afterwards (the steps after
-        // it are discarded), so no bookkeeping sits on the dependency chain.
+        // lane j records the bin after step j and whether step j was too close to call in
+        // float32, and the batch is cut at the first such step afterwards (the steps after it
+        // are discarded), so no bookkeeping sits on the dependency chain.
         // Steps are resolved in pairs (2p, 2p+1): the three cache lookups a pair can need
         // (k' of the first step; k' of the second step after the first moved / stayed) are
-        // issued together, so one shuffle latency covers two moves.  Decision variable:
+        // issued together and the second step is evaluated in both worlds, so one shuffle
+        // latency and one select cover two moves.  Decision variable:
         // e = ln g(k) - ln g(k') - thr; accept if e > M, reject if e < -M, else unsure.
-        int xk = 16; // cache offset of the current bin
-        int myx = 16; // lane j: cache offset of the bin after step j
-        float Lk = 0.0f;
-        unsigned accbits = 0u, badbits = 0u, saccbits = 0u, srejbits = 0u;
+        // A target outside the 32 cached bins reads a wrong lane; such steps are found after
+        // the loop (the target is known per lane) and cut there as well.
+        int xk = 16;       // cache offset of the current bin
+        float Lk = 0.0f;   // running value of the current bin (the cache holds it only once left)
+        int myx = 16;      // lane j: cache offset of the bin after step j
+        bool myun = false; // lane j: step j unsure in float32
+        bool mysa = false, mysr = false; // CHECK: float32 verdict of step j (sure accept / reject)
 #pragma unroll
         for (int p = 0; p < 16; ++p) {
             const int i = 2 * p;
-            if ((p & 1) == 0 && p > 0 && (badbits != 0u || i >= J)) break; // every 2 pairs (A/B)
+            if ((p & 1) == 0 && p > 0 && (i >= J || (unsigned)xk >= 32u || __any_sync(FULL, myun)))
+                break; // every 2 pairs
             const int dk0 = __shfl_sync(FULL, dk, i), dk1 = __shfl_sync(FULL, dk, i + 1);
             const float th0 = __shfl_sync(FULL, thr, i), th1 = __shfl_sync(FULL, thr, i + 1);
-            const int x0 = xk + dk0;       // k' of step i
-            const int xA = x0 + dk1;       // k' of step i+1 if step i moved
-            const int xR = xk + dk1;       // k' of step i+1 if step i stayed
+            const int x0 = xk + dk0; // k' of step i
+            const int xA = x0 + dk1; // k' of step i+1 if step i moved
+            const int xR = xk + dk1; // k' of step i+1 if step i stayed
+            const bool atk = lane == xk, at0 = lane == x0;
             const float L0 = __shfl_sync(FULL, Lw, x0 & 31);
             const float LA_ = __shfl_sync(FULL, Lw, xA & 31);
             const float LR = __shfl_sync(FULL, Lw, xR & 31);
-            // step i
-            const bool dz0 = dk0 == 0;
-            const float e0 = (Lk - L0) - th0;
-            const bool a0 = dz0 || e0 > M;
-            const bool moved0 = a0 && !dz0;
-            const bool un0 = !dz0 && (CHECK ? !(L0 == INFINITY) : !(fabsf(e0) > M));
-            const bool bad0 = (unsigned)x0 >= 32u || un0;
-            // step i+1 in the world the first step chose
             const float LA = (dk1 == -dk0) ? Lk : LA_; // back to the bin just left
             const float Lm = L0 + lnf_f;               // value after step i if moved
             const float Ls = Lk + lnf_f;               // value after step i if stayed
-            const float Lc1 = moved0 ? Lm : Ls;
-            const float L1 = moved0 ? LA : LR;
-            const int x1 = moved0 ? xA : xR;
-            const int xc1 = moved0 ? x0 : xk;
-            const bool dz1 = dk1 == 0;
-            const float e1 = (Lc1 - L1) - th1;
-            const bool a1 = dz1 || e1 > M;
-            const bool moved1 = a1 && !dz1;
-            const bool un1 = !dz1 && (CHECK ? !(L1 == INFINITY) : !(fabsf(e1) > M));
-            const bool bad1 = (unsigned)x1 >= 32u || un1;
-            // write back the running values of the bins left
-            if (moved0 && lane == xk) Lw = Lk;
-            if (moved1 && lane == xc1) Lw = Lc1;
-            xk = moved1 ? x1 : xc1;
-            if (lane == i) myx = xc1;
-            if (lane == i + 1) myx = xk;
-            Lk = (moved1 ? L1 : Lc1) + lnf_f;
-            accbits |= (a0 ? (1u << i) : 0u) | (a1 ? (2u << i) : 0u);
-            badbits |= (bad0 ? (1u << i) : 0u) | (bad1 ? (2u << i) : 0u);
-            if (CHECK) {
-                saccbits |= (e0 > M ? (1u << i) : 0u) | (e1 > M ? (2u << i) : 0u);
-                srejbits |= (e0 < -M ? (1u << i) : 0u) | (e1 < -M ? (2u << i) : 0u);
+            // step i
+            const float e0 = (Lk - L0) - th0;
+            const bool m0 = e0 > M;
+            const bool un0 = CHECK ? (th0 != INFINITY && L0 != INFINITY) : !(fabsf(e0) > M);
+            // step i+1 in both worlds, then the world step i chose
+            const float e1A = (Lm - LA) - th1;
+            const float e1R = (Ls - LR) - th1;
+            const bool m1 = m0 ? (e1A > M) : (e1R > M);
+            const float e1 = m0 ? e1A : e1R;
+            const float L1 = m0 ? LA : LR;
+            const float Lc1 = m0 ? Lm : Ls;
+            const int x1 = m0 ? xA : xR;
+            const int xc1 = m0 ? x0 : xk;
+            const bool un1 = CHECK ? (th1 != INFINITY && L1 != INFINITY) : !(fabsf(e1) > M);
+            // the bins left keep their running values
+            if (m0 && atk) Lw = Lk;
+            if (m1 && (m0 ? at0 : atk)) Lw = Lc1;
+            if (lane == i) {
+                myx = xc1;
+                myun = un0;
+                if (CHECK) {
+                    mysa = e0 > M;
+                    mysr = e0 < -M;
+                }
             }
+            xk = m1 ? x1 : xc1;
+            if (lane == i + 1) {
+                myx = xk;
+                myun = un1;
+                if (CHECK) {
+                    mysa = e1 > M;
+                    mysr = e1 < -M;
+                }
+            }
+            Lk = (m1 ? L1 : Lc1) + lnf_f;
         }
+        // bin before step j; a target outside the cache makes step j unsure as well
+        const int xup = __shfl_up_sync(FULL, myx, 1);
+        const int xbefore = lane == 0 ? 16 : xup;
+        const bool oob = (unsigned)(xbefore + dk) >= 32u;
+        const unsigned badbits = __ballot_sync(FULL, myun || oob);
         const unsigned stopbits = badbits | (J >= 32 ? 0u : (0xffffffffu << J));
         const int ndone = stopbits ? __ffs(stopbits) - 1 : 32;
         const bool amb_stop = ndone < J;
-        accbits &= ndone >= 32 ? 0xffffffffu : ((1u << ndone) - 1u);
         // bin after each step (valid for the steps done, all inside the cache)
         const int mypos = k0 - 16 + myx;
         const int kc = ndone > 0 ? k0 - 16 + __shfl_sync(FULL, myx, ndone - 1) : k0;
         // float32 verdict at the cut (CHECK): 1 sure accept, 0 sure reject, -1 unsure
-        const int scr = !CHECK || ndone >= 32 ? -1
-                        : (((saccbits >> ndone) & 1u) ? 1 : (((srejbits >> ndone) & 1u) ? 0 : -1));
+        int scr = -1;
+        if (CHECK) {
+            const unsigned sa = __ballot_sync(FULL, mysa), sr = __ballot_sync(FULL, mysr);
+            scr = ndone >= 32 ? -1 : (((sa >> ndone) & 1u) ? 1 : (((sr >> ndone) & 1u) ? 0 : -1));
+        }
 
         // ---- side effects of steps 0..ndone-1
         const bool mine = lane < ndone;
-        if (mine && ((accbits >> lane) & 1u)) sp[site] = (int8_t)snew; // conflict-free sites
-        if (mine && !frozen)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&V[mypos - lo]),
-                      (unsigned long long)lnfq);
+        const bool accj = dz || myx != xbefore; // step j accepted (a move to another bin, or dE = 0)
+        if (mine && accj) sp[site] = (int8_t)snew; // conflict-free sites
+        {
+            // visits: the lanes of one bin add their count with one plain update (no atomics)
+            const unsigned grp = __match_any_sync(FULL, mine ? mypos : -1 - lane);
+            if (mine && !frozen && lane == __ffs(grp) - 1)
+                V[mypos - lo] += (long long)__popc(grp) * lnfq;
+        }
         if (REPLAY && mine) {
-            c.acc_out[(size_t)slot * T + t + lane] = (accbits >> lane) & 1u;
+            c.acc_out[(size_t)slot * T + t + lane] = accj ? 1 : 0;
             c.dk_out[(size_t)slot * T + t + lane] = dk;
         }
-        nacc += __popc(accbits);
+        nacc += __popc(__ballot_sync(FULL, mine && accj));
         k = kc;
         t += ndone;
         __syncwarp();

@@ -90,19 +90,27 @@ def test_lnu_screen_bound_all_words(cuda_lib):
 
 
 def test_seqadd_equals_sequential_float64_loop(cuda_lib):
+    """x + f + ... + f (c additions) as the kernels rebuild ln g: dyadic and non-dyadic f (the 1/t
+    schedule), negative x (warm starts), x at binade edges, and ties (f = (a + 1/2) ulp(x))."""
     rng = np.random.default_rng(2)
-    n = 2000
-    x = np.concatenate([rng.uniform(0, 5000, n // 3), rng.uniform(-50, 50, n // 3),
-                        2.0 ** rng.integers(-5, 12, n - 2 * (n // 3)) - rng.uniform(0, 1e-3, n - 2 * (n // 3))])
-    f = np.where(rng.random(n) < 0.7, 2.0 ** -rng.integers(0, 27, n), rng.uniform(1e-9, 1e-2, n))
-    c = rng.integers(0, 2000, n).astype(np.uint32)
+    n = 3000
+    k = n // 5
+    x = np.concatenate([rng.uniform(0, 5000, k), rng.uniform(-50, 50, k),
+                        2.0 ** rng.integers(-5, 12, k) - rng.uniform(0, 1e-3, k),
+                        (2.0 ** rng.integers(-8, 14, k)) * rng.choice([-1.0, 1.0], k),
+                        rng.uniform(-3e4, 3e4, n - 4 * k)])
+    f = np.where(rng.random(n) < 0.4, 2.0 ** -rng.integers(0, 27, n),
+                 np.where(rng.random(n) < 0.5, rng.uniform(1e-9, 1e-2, n),
+                          rng.integers(1, 10 ** 4, n) / rng.integers(10 ** 6, 10 ** 11, n)))
+    ties = rng.random(n) < 0.1
+    ulp = np.spacing(np.abs(x))
+    f = np.where(ties & (x != 0), (rng.integers(0, 300, n) + 0.5) * ulp, f)
+    c = rng.integers(0, 20000, n).astype(np.uint32)
     x[:4] = [0.0, -0.0, 2047.9999999999998, -1e-12]
-    want = np.empty(n)
-    for i in range(n):
-        v = np.float64(x[i])
-        for _ in range(int(c[i])):
-            v = v + np.float64(f[i])
-        want[i] = v
+    want = x.copy()  # the additions one at a time, all cases in step
+    for step in range(int(c.max())):
+        live = step < c
+        want[live] = want[live] + f[live]
     xd, fd = torch.from_numpy(x).cuda(), torch.from_numpy(f).cuda()
     cd = torch.from_numpy(c.view(np.int32)).cuda()
     out = torch.zeros(n, dtype=torch.float64, device="cuda")
