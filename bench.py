@@ -262,13 +262,13 @@ def run_gpu_batch(args, wl, rank, world):
     descs = batch24_descs(wl, rank)
     b = R.REWLBatch(descs, interval=wl["interval"], stream=stream)
     b.init()
-    best, trial = b.autotune(rounds=1)  # 4 rounds of the simulation itself, untimed
+    best, trial = b.autotune(rounds=1)  # trial rounds of the simulation itself, untimed
     info = b.info()
     per_round = info["walkers"] * wl["interval"]
-    R = args.rounds_per_step
-    per_step = per_round * R
+    RPS = args.rounds_per_step
+    per_step = per_round * RPS
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    b.step(args.warmup * R)
+    b.step(args.warmup * RPS)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -280,7 +280,7 @@ def run_gpu_batch(args, wl, rank, world):
         for a, z in evs:
             flush.zero_()
             a.record(stream)
-            b.step(R)
+            b.step(RPS)
             z.record(stream)
         torch.cuda.synchronize()
     step_ms = sum(a.elapsed_time(z) for a, z in evs)
@@ -290,7 +290,7 @@ def run_gpu_batch(args, wl, rank, world):
     d2h = 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        b.run(max_rounds=R)
+        b.run(max_rounds=RPS)
         for i in range(len(descs)):
             x = b.instance(i).get_state("lng_mean")
             d2h += x.nbytes
@@ -303,11 +303,11 @@ def run_gpu_batch(args, wl, rank, world):
                    d["flatness"], seed=d["seed"], instance=d["instance"],
                    interval=wl["interval"], stream=stream)
         g.init()
-        g.step(args.warmup * R)
+        g.step(args.warmup * RPS)
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record(stream)
-        g.step(args.steps * R)
+        g.step(args.steps * RPS)
         z.record(stream)
         torch.cuda.synchronize()
         solo_ms += a.elapsed_time(z)
@@ -321,18 +321,18 @@ def run_gpu_batch(args, wl, rank, world):
         "data": "synthetic",
         "config": {"workload": args.workload, "instances": len(descs), "walkers": info["walkers"],
                    "interval": wl["interval"],
-                   "ctas_per_launch": info["ctas"], "autotuned_walkers_per_cta": best,
+                   "ctas_per_launch": info["ctas"], "autotuned": best,
                    "autotune_ms_per_round": trial,
                    "parallelism": f"replicas{world}" if world > 1 else "1gpu",
                    "l2": "flushed (256 MB write) before every timed step"},
         "roofline": _roofline(per_round, move_ms, move_launches, sms, step_ms, args.workload),
-        "step_work": {"rounds": R, "attempts": per_step * world},
+        "step_work": {"rounds": RPS, "attempts": per_step * world},
         "one_at_a_time": {"value": per_step * args.steps / (solo_ms / 1e3), "unit": UNIT,
                           "ms_per_step": solo_ms / args.steps},
         "e2e": {"value": attempts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h // max(args.steps, 1),
-                "call": f"rewl_batch_run({R} rounds) + rewl_get_state(lng_mean) of each instance"},
-        "gpu_launches": 4 * R * args.steps, "clocks": clk.summary(),
+                "call": f"rewl_batch_run({RPS} rounds) + rewl_get_state(lng_mean) of each instance"},
+        "gpu_launches": 4 * RPS * args.steps, "clocks": clk.summary(),
     }
 
 
@@ -680,11 +680,11 @@ def run_gpu(args, wl, rank, world):
                lnf_init=args.lnf_init)
     r.init()
     per_round = r.nw * wl["interval"]
-    R = args.rounds_per_step
-    per_step = per_round * R
+    RPS = args.rounds_per_step
+    per_step = per_round * RPS
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        r.step(R)
+        r.step(RPS)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -697,7 +697,7 @@ def run_gpu(args, wl, rank, world):
         for a, b in evs:
             flush.zero_()  # L2 flush, outside the timed events
             a.record(stream)
-            r.step(R)
+            r.step(RPS)
             b.record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -713,7 +713,7 @@ def run_gpu(args, wl, rank, world):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r.run(max_rounds=R)
+        r.run(max_rounds=RPS)
         _ = r.get_state("lng_mean")
     e2e_s = time.perf_counter() - t0
     t_max, e2e_s = max_over_ranks([step_ms, e2e_s], device="cuda")
@@ -725,16 +725,77 @@ def run_gpu(args, wl, rank, world):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
         "config": workload_config(args, wl, world),
-        "step_work": {"rounds": R, "attempts": per_step * world},
+        "step_work": {"rounds": RPS, "attempts": per_step * world},
         "roofline": _roofline(per_round, move_ms, move_launches, sms, step_ms, args.workload),
         "e2e": {"value": attempts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": lng_bytes + 48,
-                "call": f"rewl_run({R} rounds) + rewl_get_state(lng_mean) per step"},
-        "gpu_launches": 4 * R * args.steps,
+                "call": f"rewl_run({RPS} rounds) + rewl_get_state(lng_mean) per step"},
+        "gpu_launches": 4 * RPS * args.steps,
         "clocks": clocks,
         "exact_fraction": st["exact_decisions"] / max(st["attempts"], 1),
     }
     r.close()
+    return out
+
+
+def run_gpu_sharded(args, wl, rank, world):
+    """One run of the workload with its windows split over the ranks (consecutive ranges, one
+    shard per GPU; Sec. 2 exchange across shard boundaries by point-to-point transfers after
+    every round).  Strong scaling: the total work is fixed as N grows."""
+    import torch
+    import torch.distributed as dist
+    from paper_1402_2328_gb300 import shard as S
+    import paper_1402_2328_gb300.rewl as RW
+
+    ndev = torch.cuda.device_count()
+    dev = int(os.environ.get("LOCAL_RANK", "0")) % max(ndev, 1)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    seed = seed_for(wl["config_id"])
+    glo, ghi = RW.windows_layout(RW.num_bins(wl["model"], wl["L"]), wl["windows"], wl["overlap"])
+    wb, n = S.split_windows(wl["windows"], world)[rank]
+    h = S.make_shard(wl["model"], wl["L"], glo, ghi, wb, n, wl["walkers"], wl["lnf_final"],
+                     wl["flatness"], seed, interval=wl["interval"], lnf_init=args.lnf_init,
+                     stream=stream)
+    h.init()
+    d = S.DistShard(h, rank, world, torch.device("cuda", dev))
+    per_round = wl["windows"] * wl["walkers"] * wl["interval"]   # the whole run, all ranks
+    RPS = args.rounds_per_step
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    d.step(args.warmup * RPS)
+    torch.cuda.synchronize()
+    dist.barrier()
+    h.set_param("profile", 1)
+    h.kernel_time(reset=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(dev) as clk:
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            d.step(RPS)
+            b.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    step_ms = sum(a.elapsed_time(b) for a, b in evs)
+    move_ms, move_launches = h.kernel_time(reset=True)
+    h.set_param("profile", 0)
+    t_max = max_over_ranks([step_ms], device="cuda" if dist.get_backend() == "nccl" else "cpu")[0]
+    nb = len(d.bounds)
+    out = {
+        "metric": METRIC, "value": per_round * RPS * args.steps / (t_max / 1e3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
+        "config": dict(workload_config(args, wl, 1), parallelism=f"windows{world}"),
+        "step_work": {"rounds": RPS, "attempts": per_round * RPS},
+        "roofline": _roofline(h.nw * wl["interval"], move_ms, move_launches, sms, step_ms, args.workload),
+        "gpu_launches": (4 + 4 * nb) * RPS * args.steps,
+        "shards": S.split_windows(wl["windows"], world),
+        "transport": dist.get_backend(), "clocks": clk.summary(),
+    }
+    h.close()
     return out
 
 
@@ -744,6 +805,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--sharded", action="store_true",
+                    help="N > 1: split the workload's windows over the ranks (one run, strong "
+                         "scaling) instead of N independent replicas")
+    ap.add_argument("--backend", default="nccl", choices=["nccl", "gloo"],
+                    help="torch.distributed backend for N > 1 (gloo: transfers through the host)")
     ap.add_argument("--workload", default="potts10_L80_h64_m16", choices=sorted(WORKLOADS))
     ap.add_argument("--rounds-per-step", type=int, default=256,
                     help="rounds of the hot path in one timed step")
@@ -842,9 +908,13 @@ def main():
                          f"{args.cpu_rounds} rounds each ({attempts:.3g} attempts, {tmax:.1f} s)"}
     if world > 1:
         import torch
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))  # before NCCL binds a GPU
-        torch.distributed.init_process_group("nccl")
-    out = run_gpu_batch(args, wl, rank, world) if wl.get("batch") else run_gpu(args, wl, rank, world)
+        ndev = max(torch.cuda.device_count(), 1)
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")) % ndev)  # before NCCL binds a GPU
+        torch.distributed.init_process_group(args.backend)
+    if args.sharded and world > 1 and not wl.get("batch"):
+        out = run_gpu_sharded(args, wl, rank, world)
+    else:
+        out = run_gpu_batch(args, wl, rank, world) if wl.get("batch") else run_gpu(args, wl, rank, world)
     if rank == 0:
         if cpu is not None:
             out["cpu_baseline"] = cpu

@@ -74,7 +74,9 @@ int rewl_create(rewl_t *out, int model, int L, int windows, double overlap,
  * stream, default 0), "graph_rounds" (rounds per CUDA-graph replay, default 32; 0 = no
  * graph), "walkers_per_block" (warps per CTA of the move kernel; 0 = automatic: the power
  * of two covering walkers / SMs, at most 4), "check_all" (1 = decide every move with the
- * float64 path as well and count disagreements; diagnostic), "schedule" (0 = ln f halving,
+ * float64 path as well and count disagreements; diagnostic), "layout" (move kernel: 0 = one
+ * warp per walker, the default; 1 = one thread per walker, for small lattices with many
+ * walkers; both give identical results), "schedule" (0 = ln f halving,
  * f -> sqrt f, Sec. 2; 1 = the 1/t schedule of Belardinelli and Pereyra, an alternative
  * Sec. 2 allows: after a halving, once ln f < 1/t with t = moves per walker / visited bins
  * of the window, ln f = 1/t is recomputed at every check, where the m walkers' ln g are
@@ -110,6 +112,14 @@ int rewl_set_lng_init(rewl_t r, const double *lng_bins, int n);
  * Used for run-time balanced splitting (Fig. 1b) and learned window boundaries.
  */
 int rewl_set_windows(rewl_t r, const int *lo_hi, int h);
+
+/*
+ * rewl_windows_equal -- the equal-size layout of Fig. 1a that rewl_create uses (the formula
+ * given there), for B+1 bins, h windows and overlap fraction `overlap`, into host lo_hi (2*h
+ * ints: lo[0..h-1] then hi[0..h-1]).  Host only, no device call.  INVALID_ARG when adjacent
+ * windows would not overlap.
+ */
+int rewl_windows_equal(int B, int h, double overlap, int *lo_hi);
 
 /*
  * rewl_windows_balanced -- run-time balanced windows (Fig. 1b).  host cost[B+1] >= 0 is the
@@ -231,6 +241,47 @@ int rewl_dims(rewl_t r, int *out);
 int rewl_get_state(rewl_t r, const char *field, void *out, size_t bytes);
 int rewl_set_state(rewl_t r, const char *field, const void *in, size_t bytes);
 
+/*
+ * Window-sharded runs (Sec. 2: walkers in different energy windows only meet in the exchange
+ * of Eq. (1), between neighbouring windows).  A run over h_global windows is split into
+ * shards of consecutive windows, one handle each (typically one per GPU); the handles' state
+ * together equals that of one handle over all windows, round for round, bit for bit.
+ *
+ * rewl_set_shard -- before rewl_init, on a handle made by rewl_create with `windows` = the
+ * number of windows of this shard: lo_hi (host, 2 h_global ints: lo[0..h-1] then hi[0..h-1])
+ * is the global layout (lo[0] = 0, hi[h-1] = B, adjacent windows overlapping) and the shard
+ * holds windows w_begin .. w_begin + windows - 1.  Random streams use global window and walker
+ * indices.  A shard never ends a run by itself (it behaves as with "production" = 1): the
+ * caller ends the run when every shard reports all its windows finished (rewl_stats).
+ * INVALID_ARG for a bad layout or range; STATE after rewl_init.
+ *
+ * After every round (rewl_step(r, 1) on every shard), the pair of windows across each shard
+ * boundary exchanges through four calls on each side and three transfers the caller makes
+ * (any transport: NCCL, MPI, host copies).  side 1 = this shard's last window (the pair's
+ * lower window), side 0 = its first window (the pair's upper window).  In a round where that
+ * pair does not exchange (round parity) the calls are still made and change nothing.  All
+ * buffers are device memory of the handle's device; work goes to the handle's stream:
+ *   rewl_boundary_bins(side, bins)                    bins: out, m int32 (the side's walkers' bins)
+ *     -> send bins to the partner shard, receive its bins as partner_bins
+ *   rewl_boundary_half(side, partner_bins, half)      half: out, m float64 (this side's term of ln P
+ *                                                     for each partner pair i; NaN: cannot exchange)
+ *     -> send half, receive the partner's as partner_half
+ *   rewl_boundary_decide(side, half, partner_half, accepted, lattices)
+ *                                                     accepted: out, m uint8 (same on both sides);
+ *                                                     lattices: out, m x N int8, the lattices this
+ *                                                     side hands over (rows of accepted pairs)
+ *     -> send lattices, receive the partner's as partner_lattices
+ *   rewl_boundary_import(side, partner_bins, accepted, partner_lattices)
+ * STATE if the handle is not an initialised shard; INVALID_ARG for a side without a neighbour.
+ */
+int rewl_set_shard(rewl_t r, const int *lo_hi, int h_global, int w_begin);
+int rewl_boundary_bins(rewl_t r, int side, int *bins);
+int rewl_boundary_half(rewl_t r, int side, const int *partner_bins, double *half);
+int rewl_boundary_decide(rewl_t r, int side, const double *half, const double *partner_half,
+                         uint8_t *accepted, int8_t *lattices);
+int rewl_boundary_import(rewl_t r, int side, const int *partner_bins, const uint8_t *accepted,
+                         const int8_t *partner_lattices);
+
 /* Run statistics (Sec. 2 exchange acceptance; Eq. 5 step counts). */
 typedef struct {
     long long rounds;            /* rounds executed */
@@ -316,7 +367,9 @@ typedef struct {
 
 /* n instances (host array of descriptors), all with the same moves-per-round `interval`. */
 int rewl_batch_create(rewl_batch_t *out, const rewl_desc_t *descs, int n, long long interval);
-/* Keys: "walkers_per_block" (upper bound of walkers per CTA, 0 = automatic), "graph_rounds",
+/* Keys: "walkers_per_block" (upper bound of warps per CTA, 0 = automatic),
+ * "thread_layout_max_sites" (instances with at most this many sites run one thread per walker,
+ * up to 32 x walkers_per_block walkers per CTA; 0 = none, the default), "graph_rounds",
  * "profile" (time the move kernel with events, rewl_batch_kernel_time), "check_all",
  * "prep_budget" (before init). */
 int rewl_batch_set_param(rewl_batch_t b, const char *key, double value);
@@ -328,18 +381,26 @@ int rewl_batch_step(rewl_batch_t b, int rounds);
 /* Run until every instance is done, max_rounds (< 0: no limit) or max_seconds (<= 0: none). */
 int rewl_batch_run(rewl_batch_t b, double max_seconds, long long max_rounds, int *status);
 /*
- * Autotuner: times `rounds` rounds with each walkers-per-CTA bound in {2, 4, 8, 16} and keeps
- * the fastest.  The trial rounds are ordinary rounds of the simulation (results do not depend
- * on the launch configuration).  best (may be NULL) gets the choice, ms (may be NULL, 4
- * doubles) the measured milliseconds per round of each candidate.
+ * Autotuner.  First it times `rounds` rounds for every pair of a walkers-per-CTA bound in
+ * {2, 4, 8, 16} and a thread-per-walker site limit in {0, 400, 1024, 1600} (which instances run
+ * one thread per walker, hence how many windows of an instance share a CTA), and keeps the
+ * fastest; then, with that layout, it times one CUDA-graph replay of each length in
+ * {8, 32, 128} rounds (the kernel schedule between exchanges) and keeps the fastest.  The
+ * trial rounds are ordinary rounds of the simulation (results do not depend on the launch
+ * configuration).  best (may be NULL, 3 ints) gets walkers per CTA, site limit and graph
+ * rounds; ms (may be NULL, REWL_BATCH_TUNE_CANDIDATES doubles) the milliseconds per round of
+ * each candidate, index 4 * (site-limit index) + (walkers index), then the three graph
+ * lengths; -1 for a site limit no instance falls under (the same layout as limit 0).
  */
+#define REWL_BATCH_TUNE_CANDIDATES 19
 int rewl_batch_autotune(rewl_batch_t b, int rounds, int *best, double *ms);
 /* Instance i as a handle for the query calls (get_state, get_lng, stitch, stats,
  * checkpoint); owned by the batch: do not destroy it or run it on its own.  Before
  * rewl_batch_init, rewl_set_windows on it replaces the instance's window layout (e.g. run-time
  * balanced windows, Fig. 1b). */
 int rewl_batch_instance(rewl_batch_t b, int i, rewl_t *out);
-/* out (4 ints): instances, total walkers, CTAs of the move launch, warps per CTA. */
+/* out (6 ints): instances, total walkers, CTAs of the move launch, warps per CTA,
+ * thread-per-walker site limit, rounds per graph replay. */
 int rewl_batch_info(rewl_batch_t b, int *out);
 int rewl_batch_kernel_time(rewl_batch_t b, double *move_ms, long long *launches, int reset);
 void rewl_batch_destroy(rewl_batch_t b);

@@ -22,6 +22,7 @@ struct rewl_batch_s {
     std::vector<rewl_t> inst;
     long long interval = 10000;
     int wpb = 0; // 0: automatic
+    int thread_sites = 0; // instances with at most this many sites run one thread per walker
     int graph_rounds = 32, check_all = 0, profile = 0;
     bool inited = false;
     cudaStream_t stream = nullptr;
@@ -30,7 +31,7 @@ struct rewl_batch_s {
     int4 *d_jobs = nullptr;
     int2 *d_chk = nullptr, *d_swp = nullptr;
     double2 *d_prm = nullptr;
-    int njobs = 0, nchk = 0, nswp = 0, block_walkers = 1;
+    int njobs = 0, nchk = 0, nswp = 0, block_walkers = 1, wpb_used = 4;
     size_t smem = 0;
     std::vector<DevStatus> hst;
     DevStatus *h_status = nullptr; // pinned, one per instance
@@ -68,8 +69,10 @@ static void free_tables(rewl_batch_t b)
     b->d_prm = nullptr;
 }
 
-// Job grid for a given walkers-per-CTA bound; larger lattices first.
-static int build_jobs(rewl_batch_t b, int wpb)
+// Job grid for a given walkers-per-CTA bound; larger lattices first.  Instances with at most
+// `thread_sites` sites run one thread per walker: their CTAs take up to 32 x (warps per CTA)
+// walkers, as many as shared memory holds (job.x carries the layout in bit 24).
+static int build_jobs(rewl_batch_t b, int wpb, int thread_sites)
 {
     const int n = (int)b->inst.size();
     std::vector<int> order(n);
@@ -78,14 +81,34 @@ static int build_jobs(rewl_batch_t b, int wpb)
         return move_smem_per_walker(b->inst[x]->N, b->inst[x]->W) >
                move_smem_per_walker(b->inst[y]->N, b->inst[y]->W);
     });
-    std::vector<int4> jobs;
+    auto threaded = [&](const rewl_t r) { return r->N <= thread_sites; };
+    // warps per CTA: the bound, lowered where a warp-per-walker lattice needs it
     int gmax = 1;
+    bool any_warp = false;
+    for (int i : order) {
+        const rewl_t r = b->inst[i];
+        if (threaded(r)) continue;
+        any_warp = true;
+        const size_t per = move_smem_per_walker(r->N, r->W);
+        gmax = std::max(gmax, std::max(1, std::min(wpb, (int)(MAX_SMEM_PER_CTA / per))));
+    }
+    if (!any_warp) gmax = wpb;
+    std::vector<int4> jobs;
     size_t smem = 0;
     for (int i : order) {
         const rewl_t r = b->inst[i];
+        if (threaded(r)) {
+            const size_t per = move_smem_per_thread_walker(r->N, r->W);
+            const int g = std::max(1, std::min(32 * gmax, (int)(MAX_SMEM_PER_CTA / per)));
+            for (int s0 = 0; s0 < r->nw; s0 += g) {
+                const int cnt = std::min(g, r->nw - s0);
+                jobs.push_back(make_int4(i | (1 << 24), s0, cnt, 0));
+                smem = std::max(smem, (size_t)cnt * per);
+            }
+            continue;
+        }
         const size_t per = move_smem_per_walker(r->N, r->W);
-        int g = std::max(1, std::min(wpb, (int)(MAX_SMEM_PER_CTA / per)));
-        gmax = std::max(gmax, g);
+        const int g = std::max(1, std::min(wpb, (int)(MAX_SMEM_PER_CTA / per)));
         for (int s0 = 0; s0 < r->nw; s0 += g) {
             const int cnt = std::min(g, r->nw - s0);
             jobs.push_back(make_int4(i, s0, cnt, 0));
@@ -101,6 +124,8 @@ static int build_jobs(rewl_batch_t b, int wpb)
     b->njobs = (int)jobs.size();
     b->block_walkers = gmax;
     b->smem = smem;
+    b->wpb_used = wpb;
+    b->thread_sites = thread_sites;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     return REWL_OK;
@@ -216,7 +241,11 @@ int rewl_batch_set_param(rewl_batch_t b, const char *key, double v)
     const std::string k(key);
     if (k == "walkers_per_block" && v >= 0 && v <= 16) {
         b->wpb = (int)v;
-        return b->inited ? build_jobs(b, b->wpb > 0 ? b->wpb : auto_wpb(b)) : REWL_OK;
+        return b->inited ? build_jobs(b, b->wpb > 0 ? b->wpb : auto_wpb(b), b->thread_sites) : REWL_OK;
+    }
+    if (k == "thread_layout_max_sites" && v >= 0 && v <= 65536) {
+        b->thread_sites = (int)v;
+        return b->inited ? build_jobs(b, b->wpb > 0 ? b->wpb : auto_wpb(b), b->thread_sites) : REWL_OK;
     }
     if (k == "graph_rounds" && v >= 0 && v <= 4096) {
         b->graph_rounds = (int)v;
@@ -286,7 +315,7 @@ int rewl_batch_init(rewl_batch_t b)
     if (e != cudaSuccess) return b->cuda_fail(e, "rewl_batch_init tables");
     b->nchk = (int)chk.size();
     b->nswp = (int)swp.size();
-    const int rc = build_jobs(b, b->wpb > 0 ? b->wpb : auto_wpb(b));
+    const int rc = build_jobs(b, b->wpb > 0 ? b->wpb : auto_wpb(b), b->thread_sites);
     if (rc != REWL_OK) return rc;
     b->inited = true;
     b->seconds = 0.0;
@@ -401,44 +430,78 @@ int rewl_batch_autotune(rewl_batch_t b, int rounds, int *best, double *ms)
         if (rc != REWL_OK) return rc;
     }
     // the trial rounds are rounds of the simulation itself: results do not depend on the
-    // launch configuration, so timing candidates costs nothing but the choice
-    const int cand[4] = {2, 4, 8, 16};
+    // launch configuration, so timing candidates costs nothing but the choice.
+    // 1) layout x walkers per CTA: per-round time of `rounds` rounds for every pair
+    static const int wcand[4] = {2, 4, 8, 16};
+    static const int tcand[4] = {0, 400, 1024, 1600};
+    static const int gcand[3] = {8, 32, 128};
     double bestms = 1e300;
-    int bestg = 4;
+    int bestg = 4, bestt = 0, bestgr = b->graph_rounds;
     cudaEvent_t a = nullptr, z = nullptr;
     cudaError_t e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&z);
     if (e != cudaSuccess) return b->cuda_fail(e, "autotune events");
     int rc = REWL_OK;
-    for (int ci = 0; ci < 4 && rc == REWL_OK; ++ci) {
-        rc = build_jobs(b, cand[ci]);
-        if (rc != REWL_OK) break;
-        const int prof = b->profile;
-        b->profile = 0;
-        e = cudaEventRecord(a, b->stream);
-        for (int i = 0; i < rounds && e == cudaSuccess; ++i) e = enqueue_batch_round(b);
-        if (e == cudaSuccess) e = cudaEventRecord(z, b->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(z);
-        b->profile = prof;
-        float t = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, z);
-        if (e != cudaSuccess) {
-            rc = b->cuda_fail(e, "autotune");
-            break;
+    const int prof = b->profile;
+    b->profile = 0;
+    auto timed = [&](int nrounds, bool graph, double *per) -> int {
+        cudaError_t e2 = cudaEventRecord(a, b->stream);
+        if (graph) {
+            for (int i = 0; i < nrounds / b->graph_len && e2 == cudaSuccess; ++i)
+                e2 = cudaGraphLaunch(b->graph, b->stream);
+        } else {
+            for (int i = 0; i < nrounds && e2 == cudaSuccess; ++i) e2 = enqueue_batch_round(b);
         }
-        const double per = (double)t / rounds;
-        if (ms) ms[ci] = per;
-        if (per < bestms) {
-            bestms = per;
-            bestg = cand[ci];
+        if (e2 == cudaSuccess) e2 = cudaEventRecord(z, b->stream);
+        if (e2 == cudaSuccess) e2 = cudaEventSynchronize(z);
+        float t = 0.f;
+        if (e2 == cudaSuccess) e2 = cudaEventElapsedTime(&t, a, z);
+        if (e2 != cudaSuccess) return b->cuda_fail(e2, "autotune");
+        *per = (double)t / nrounds;
+        return REWL_OK;
+    };
+    int ci = 0;
+    for (int ti = 0; ti < 4 && rc == REWL_OK; ++ti)
+        for (int wi = 0; wi < 4 && rc == REWL_OK; ++wi, ++ci) {
+            bool any_thread = false;
+            for (rewl_t r : b->inst) any_thread |= r->N <= tcand[ti];
+            double per = 1e300;
+            if (ti == 0 || any_thread) { // a threshold no instance reaches repeats candidate ti = 0
+                rc = build_jobs(b, wcand[wi], tcand[ti]);
+                if (rc == REWL_OK) rc = timed(rounds, false, &per);
+            }
+            if (ms) ms[ci] = per < 1e300 ? per : -1.0;
+            if (rc == REWL_OK && per < bestms) {
+                bestms = per;
+                bestg = wcand[wi];
+                bestt = tcand[ti];
+            }
+        }
+    // 2) rounds per CUDA-graph replay, with the chosen layout
+    if (rc == REWL_OK) rc = build_jobs(b, bestg, bestt);
+    double bestgms = 1e300;
+    for (int gi = 0; gi < 3 && rc == REWL_OK; ++gi, ++ci) {
+        rc = build_batch_graph(b, gcand[gi]);
+        double per = 1e300;
+        if (rc == REWL_OK) rc = timed(gcand[gi], true, &per);
+        if (ms) ms[ci] = rc == REWL_OK ? per : -1.0;
+        if (rc == REWL_OK && per < bestgms) {
+            bestgms = per;
+            bestgr = gcand[gi];
         }
     }
+    b->profile = prof;
     cudaEventDestroy(a);
     cudaEventDestroy(z);
     if (rc != REWL_OK) return rc;
     b->wpb = bestg;
-    if (best) *best = bestg;
-    return build_jobs(b, bestg);
+    b->graph_rounds = bestgr;
+    if (best) {
+        best[0] = bestg;
+        best[1] = bestt;
+        best[2] = bestgr;
+    }
+    return build_jobs(b, bestg, bestt);
 }
 
 int rewl_batch_instance(rewl_batch_t b, int i, rewl_t *out)
@@ -457,6 +520,8 @@ int rewl_batch_info(rewl_batch_t b, int *out)
     out[1] = (int)nw;
     out[2] = b->njobs;
     out[3] = b->block_walkers;
+    out[4] = b->thread_sites;
+    out[5] = b->graph_rounds;
     return REWL_OK;
 }
 

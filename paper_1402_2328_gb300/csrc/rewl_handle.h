@@ -20,6 +20,11 @@ struct rewl_s {
     uint32_t inst = 0;
     long long interval = 10000, prep_budget = 100;
     int graph_rounds = 32, wpb = 0, check_all = 0, profile = 0, schedule = 0, production = 0;
+    int layout = 0; // move kernel: 0 one warp per walker, 1 one thread per walker
+    // window-sharded run: global index of this handle's first window, and the bins of the
+    // neighbouring shards' boundary windows (lo, hi of window w_begin-1, then of w_end; -1: none)
+    int shard = 0, w_begin = 0;
+    int nbr[4] = {-1, -1, -1, -1};
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free; // move-kernel timing
     std::vector<int> lo, hi;
     std::vector<double> lng_init;

@@ -89,6 +89,17 @@ static int walkers_per_block(const rewl_t r)
     return g;
 }
 
+// walkers (threads) per CTA of the thread-per-walker layout: whole warps, spread over the SMs,
+// at most 128 and what shared memory holds
+static int thread_walkers_per_block(const rewl_t r)
+{
+    const size_t per = move_smem_per_thread_walker(r->N, r->W);
+    int g = (r->nw + r->sms - 1) / r->sms;
+    g = std::min(128, std::max(32, (g + 31) & ~31));
+    while (g > 1 && (size_t)g * per > MAX_SMEM_PER_CTA) --g;
+    return g;
+}
+
 static void release(rewl_t r)
 {
     if (r->graph) cudaGraphExecDestroy(r->graph);
@@ -121,6 +132,8 @@ static int allocate(rewl_t r)
     const size_t nw = (size_t)r->nw, W = (size_t)r->W, h = (size_t)r->h;
     s.model = r->model;
     s.production = r->production;
+    s.w0 = r->w_begin;
+    s.slot0 = r->w_begin * r->m;
     s.q = r->q;
     s.L = r->L;
     s.N = r->N;
@@ -229,6 +242,8 @@ int rewl_set_param(rewl_t r, const char *key, double v)
         return REWL_OK;
     }
     if (k == "production" && (v == 0 || v == 1)) {
+        if (r->shard && v == 0)
+            return r->fail(REWL_ERR_INVALID_ARG, "production: a shard never ends a run by itself");
         r->production = (int)v;
         r->st.production = (int)v;
         if (r->graph) cudaGraphExecDestroy(r->graph);
@@ -270,6 +285,7 @@ int rewl_set_param(rewl_t r, const char *key, double v)
     else if (k == "graph_rounds" && v >= 0 && v <= 4096) r->graph_rounds = (int)v;
     else if (k == "walkers_per_block" && v >= 0 && v <= 16) r->wpb = (int)v;
     else if (k == "check_all" && (v == 0 || v == 1)) r->check_all = (int)v;
+    else if (k == "layout" && (v == 0 || v == 1)) r->layout = (int)v;
     else if (k == "schedule" && (v == 0 || v == 1)) r->schedule = (int)v;
     else return r->fail(REWL_ERR_INVALID_ARG, "rewl_set_param: unknown key or bad value: " + k);
     if (k == "instance") r->st.inst = r->inst;
@@ -302,6 +318,7 @@ int rewl_set_windows(rewl_t r, const int *lo_hi, int h)
 {
     if (!r || !lo_hi || h < 1) return REWL_ERR_INVALID_ARG;
     if (r->inited) return r->fail(REWL_ERR_STATE, "rewl_set_windows after rewl_init");
+    if (r->shard) return r->fail(REWL_ERR_STATE, "rewl_set_windows on a shard (use rewl_set_shard)");
     std::vector<int> lo(lo_hi, lo_hi + h), hi(lo_hi + h, lo_hi + 2 * h);
     if (check_windows(r->B, lo, hi) != 0)
         return r->fail(REWL_ERR_INVALID_ARG, "rewl_set_windows: invalid layout");
@@ -309,6 +326,79 @@ int rewl_set_windows(rewl_t r, const int *lo_hi, int h)
     r->lo = lo;
     r->hi = hi;
     return allocate(r);
+}
+
+int rewl_set_shard(rewl_t r, const int *lo_hi, int h_global, int w_begin)
+{
+    if (!r || !lo_hi || h_global < 2) return REWL_ERR_INVALID_ARG;
+    if (r->inited) return r->fail(REWL_ERR_STATE, "rewl_set_shard after rewl_init");
+    const int hl = r->shard ? (int)r->lo.size() : r->h;
+    std::vector<int> lo(lo_hi, lo_hi + h_global), hi(lo_hi + h_global, lo_hi + 2 * h_global);
+    if (check_windows(r->B, lo, hi) != 0)
+        return r->fail(REWL_ERR_INVALID_ARG, "rewl_set_shard: invalid global layout");
+    if (w_begin < 0 || w_begin + hl > h_global || hl >= h_global)
+        return r->fail(REWL_ERR_INVALID_ARG, "rewl_set_shard: windows outside the global layout");
+    if ((long long)h_global * r->m > (1LL << 24)) return r->fail(REWL_ERR_INVALID_ARG, "too many walkers");
+    r->lo.assign(lo.begin() + w_begin, lo.begin() + w_begin + hl);
+    r->hi.assign(hi.begin() + w_begin, hi.begin() + w_begin + hl);
+    const int we = w_begin + hl;
+    r->nbr[0] = w_begin > 0 ? lo[w_begin - 1] : -1;
+    r->nbr[1] = w_begin > 0 ? hi[w_begin - 1] : -1;
+    r->nbr[2] = we < h_global ? lo[we] : -1;
+    r->nbr[3] = we < h_global ? hi[we] : -1;
+    r->shard = 1;
+    r->w_begin = w_begin;
+    r->production = 1; // only the caller sees every shard: it decides when the run ends
+    return allocate(r);
+}
+
+static int bnd_check(rewl_t r, int side)
+{
+    if (!r->shard) return r->fail(REWL_ERR_STATE, "boundary exchange: not a shard (rewl_set_shard)");
+    if (!r->inited) return r->fail(REWL_ERR_STATE, "boundary exchange before rewl_init");
+    if (side != 0 && side != 1) return r->fail(REWL_ERR_INVALID_ARG, "boundary exchange: side must be 0 or 1");
+    if (r->nbr[2 * side] < 0)
+        return r->fail(REWL_ERR_INVALID_ARG, "boundary exchange: no neighbouring shard on that side");
+    return REWL_OK;
+}
+
+int rewl_boundary_bins(rewl_t r, int side, int *bins)
+{
+    if (!r || !bins) return REWL_ERR_INVALID_ARG;
+    int rc = bnd_check(r, side);
+    if (rc != REWL_OK) return rc;
+    cudaError_t e = launch_bnd_bins(r->st, side, bins, r->stream);
+    return e == cudaSuccess ? REWL_OK : r->cuda_fail(e, "rewl_boundary_bins");
+}
+
+int rewl_boundary_half(rewl_t r, int side, const int *partner_bins, double *half)
+{
+    if (!r || !partner_bins || !half) return REWL_ERR_INVALID_ARG;
+    int rc = bnd_check(r, side);
+    if (rc != REWL_OK) return rc;
+    const int plo = side ? r->nbr[2] : r->nbr[0], phi = side ? r->nbr[3] : r->nbr[1];
+    cudaError_t e = launch_bnd_half(r->st, side, plo, phi, partner_bins, half, r->stream);
+    return e == cudaSuccess ? REWL_OK : r->cuda_fail(e, "rewl_boundary_half");
+}
+
+int rewl_boundary_decide(rewl_t r, int side, const double *half, const double *partner_half,
+                         uint8_t *accepted, int8_t *lattices)
+{
+    if (!r || !half || !partner_half || !accepted || !lattices) return REWL_ERR_INVALID_ARG;
+    int rc = bnd_check(r, side);
+    if (rc != REWL_OK) return rc;
+    cudaError_t e = launch_bnd_decide(r->st, side, half, partner_half, accepted, lattices, r->stream);
+    return e == cudaSuccess ? REWL_OK : r->cuda_fail(e, "rewl_boundary_decide");
+}
+
+int rewl_boundary_import(rewl_t r, int side, const int *partner_bins, const uint8_t *accepted,
+                         const int8_t *partner_lattices)
+{
+    if (!r || !partner_bins || !accepted || !partner_lattices) return REWL_ERR_INVALID_ARG;
+    int rc = bnd_check(r, side);
+    if (rc != REWL_OK) return rc;
+    cudaError_t e = launch_bnd_import(r->st, side, partner_bins, accepted, partner_lattices, r->stream);
+    return e == cudaSuccess ? REWL_OK : r->cuda_fail(e, "rewl_boundary_import");
 }
 
 int rewl_set_stream(rewl_t r, void *stream)
@@ -384,7 +474,8 @@ cudaError_t rewl_enqueue_round(rewl_t r)
 {
     MoveCfg c{};
     c.T = (int)r->interval;
-    c.walkers_per_block = walkers_per_block(r);
+    c.layout = r->layout;
+    c.walkers_per_block = r->layout ? thread_walkers_per_block(r) : walkers_per_block(r);
     c.check_all = r->check_all;
     c.eps_l = LNU32_EPS;
     cudaError_t e = cudaSuccess;
@@ -579,6 +670,24 @@ int rewl_jackknife(rewl_t r, double *err, int cap, int norm)
     if (e != cudaSuccess) return r->cuda_fail(e, "rewl_jackknife");
     for (int ok : oks)
         if (!ok) return r->fail(REWL_ERR_NOT_CONVERGED, "rewl_jackknife: a resample cannot be joined");
+    return REWL_OK;
+}
+
+int rewl_windows_equal(int B, int h, double overlap, int *lo_hi)
+{
+    if (!lo_hi || B < 1 || h < 1) {
+        g_err = "rewl_windows_equal: invalid argument";
+        return REWL_ERR_INVALID_ARG;
+    }
+    std::vector<int> lo, hi;
+    if (make_windows(B, h, overlap, lo, hi) != 0) {
+        g_err = "rewl_windows_equal: windows do not overlap (too many windows or bad overlap)";
+        return REWL_ERR_INVALID_ARG;
+    }
+    for (int w = 0; w < h; ++w) {
+        lo_hi[w] = lo[w];
+        lo_hi[h + w] = hi[w];
+    }
     return REWL_OK;
 }
 

@@ -108,18 +108,27 @@ __device__ __forceinline__ uint32_t visits(const long long *V, const double *gln
     return (uint32_t)((V[b] - __double2ll_rn(__dmul_rn(glng[b], 0x1p32))) / lnfq);
 }
 
-// Float64 decision from the exact values (rare).  All lanes take part.
-__device__ __noinline__ bool exact_decision(const double *glng, const long long *V, int lo, int k,
-                                            int kp, double lnf, long long lnfq, bool frozen,
-                                            uint32_t w2)
+// Float64 decision from the exact values (rare): ln g of bins k and k' rebuilt by seqadd from
+// the launch-start values and the visits recorded in the shadow.
+__device__ __noinline__ bool exact_value_decision(const double *glng, const long long *V, int lo,
+                                                  int k, int kp, double lnf, long long lnfq,
+                                                  bool frozen, uint32_t w2)
 {
-    __syncwarp();
     const uint32_t vk = frozen ? 0u : visits(V, glng, k - lo, lnfq);
     const uint32_t vkp = frozen ? 0u : visits(V, glng, kp - lo, lnfq);
     const double lk = seqadd(glng[k - lo], lnf, vk);
     const double lkp = seqadd(glng[kp - lo], lnf, vkp);
     const double d = __dsub_rn(lk, lkp);
     return (d >= 0.0) || (lnu64(w2) < d);
+}
+
+// The same, for the warp of one walker: every lane takes part after the lanes' shadow updates.
+__device__ __forceinline__ bool exact_decision(const double *glng, const long long *V, int lo, int k,
+                                               int kp, double lnf, long long lnfq, bool frozen,
+                                               uint32_t w2)
+{
+    __syncwarp();
+    return exact_value_decision(glng, V, lo, k, kp, lnf, lnfq, frozen, w2);
 }
 
 // One walker's `c.T` moves; `base` is the walker's shared-memory block, the whole warp calls.
@@ -235,8 +244,8 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
             }
         } else {
             const unsigned long long sn = st0 + (unsigned long long)(t + lane);
-            const u32x4 r = philox((uint32_t)sn, (uint32_t)(sn >> 32), (uint32_t)slot, tag,
-                                   s.key0, s.key1);
+            const u32x4 r = philox((uint32_t)sn, (uint32_t)(sn >> 32), (uint32_t)(s.slot0 + slot),
+                                   tag, s.key0, s.key1);
             w0 = r.x;
             w1 = r.y;
             w2 = r.z;
@@ -449,6 +458,147 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// One thread per walker (small lattices, many walkers): the plain sequential walk of Sec. 2.
+// ln g is the same int64 shadow as above (multiples of 2^-32, exact visit counts), held in
+// shared memory; the current bin's value stays in registers.  Each decision is screened in
+// fixed point: D = V(k) - V(k') against ln u 2^32 (the float32 value, converted exactly up to
+// one unit), accepted or rejected when |D - ln u 2^32| exceeds the margin Mq that bounds the
+// shadow error, the float32 ln u error and the float64 rounding of ln g(k) - ln g(k'); inside
+// the margin the float64 values are rebuilt (rare).  No float arithmetic in the loop, no
+// warp cooperation: the 32 walkers of a warp run in lockstep, each on its own data.
+// ---------------------------------------------------------------------------------------
+template <bool ISING, bool REPLAY, bool CHECK>
+__device__ __forceinline__ void move_walker_thread(const State &s, const MoveCfg &c, const int slot,
+                                                   unsigned char *base)
+{
+    if (s.status != nullptr && s.status->done) return;
+    int8_t *sp = reinterpret_cast<int8_t *>(base);
+    long long *V = reinterpret_cast<long long *>(base + pad16(s.N));
+    const int w = slot / s.m;
+    const int lo = s.lo[w], hi = s.hi[w], nb = hi - lo + 1;
+    int k = s.k[slot];
+    if (lo < 0 || nb < 1 || nb > s.W || k < lo || k > hi) {
+        atomicOr(&s.status->err, ERR_INPUT);
+        return;
+    }
+    const double lnf = s.lnf[w];
+    const bool frozen = s.finished[w] != 0;
+    const int cfg = s.cfg ? s.cfg[slot] : slot;
+    int8_t *gsp = s.spins + (size_t)cfg * s.spin_stride;
+    double *glng = s.lng + (size_t)slot * s.W;
+    uint32_t *gH = s.H + (size_t)slot * s.W;
+    const Lattice lat{s.L, s.N, s.magic};
+    const int T = c.T;
+    if (s.vec_spins) {
+        const int4 *src = reinterpret_cast<const int4 *>(gsp);
+        int4 *dst = reinterpret_cast<int4 *>(sp);
+        for (int i = 0; i < (s.N >> 4); ++i) dst[i] = src[i];
+    } else {
+        for (int i = 0; i < s.N; ++i) sp[i] = gsp[i];
+    }
+    double mx = 0.0;
+    bool bad = false;
+    for (int b = 0; b < nb; ++b) {
+        const double x = glng[b];
+        bad = bad || !(fabs(x) < 0x1p30);
+        mx = fmax(mx, fabs(x));
+        V[b] = bad ? 0LL : __double2ll_rn(__dmul_rn(x, 0x1p32));
+    }
+    const bool lnf_ok = frozen || (lnf >= 0x1p-32 && lnf < 0x1p20 && mx + (double)T * lnf < 0x1p30);
+    if (bad || !lnf_ok) {
+        atomicOr(&s.status->err, ERR_RANGE);
+        return;
+    }
+    const long long lnfq = frozen ? 0LL : __double2ll_rn(__dmul_rn(lnf, 0x1p32));
+    // margin in units of 2^-32: both shadow values, the float32 ln u, the float64 difference
+    // of ln g values below 2^31 (half an ulp, 2^-22) and the conversion of ln u (one unit)
+    const long long Mq = (long long)(2.0 * shadow_error(mx, T, lnf, frozen) + (c.eps_l + 0x1p-21) * 0x1p32) + 4;
+    const unsigned long long st0 = s.step[slot];
+    const uint32_t tag = (s.inst << 8) | TAG_MOVE;
+    unsigned int nacc = 0, nex = 0, nmis = 0;
+    long long Vk = V[k - lo];
+    for (int t = 0; t < T; ++t) {
+        uint32_t w0, w1, w2;
+        if (REPLAY) {
+            const uint32_t *wp = c.words + ((size_t)slot * T + t) * 3;
+            w0 = wp[0];
+            w1 = wp[1];
+            w2 = wp[2];
+        } else {
+            const unsigned long long sn = st0 + (unsigned long long)t;
+            const u32x4 r = philox((uint32_t)sn, (uint32_t)(sn >> 32), (uint32_t)(s.slot0 + slot),
+                                   tag, s.key0, s.key1);
+            w0 = r.x;
+            w1 = r.y;
+            w2 = r.z;
+        }
+        const int site = (int)mulhi(w0, (uint32_t)s.N);
+        const int pr = ISING ? 0 : (int)mulhi(w1, (uint32_t)(s.q - 1));
+        int snew;
+        const int dk = propose_dk<ISING>(sp, lat, s.q, site, pr, snew);
+        const int kp = k + dk;
+        bool acc = dk == 0;
+        if (!acc && kp >= lo && kp <= hi) {
+            const long long e = (Vk - V[kp - lo]) - (long long)__float2ll_rz(lnu32(w2) * 0x1p32f);
+            const int scr = e > Mq ? 1 : (e < -Mq ? 0 : -1);
+            if (scr >= 0 && !CHECK) {
+                acc = scr == 1;
+            } else {
+                V[k - lo] = Vk;
+                acc = exact_value_decision(glng, V, lo, k, kp, lnf, lnfq, frozen, w2);
+                if (scr < 0) ++nex;
+                else if ((int)acc != scr) ++nmis;
+            }
+        }
+        if (acc) {
+            sp[site] = (int8_t)snew;
+            if (dk != 0) {
+                V[k - lo] = Vk;
+                k = kp;
+                Vk = V[k - lo];
+            }
+            ++nacc;
+        }
+        Vk += lnfq; // ln g(k) += ln f, H(k)++: one visit of the current bin
+        if (REPLAY) {
+            c.acc_out[(size_t)slot * T + t] = acc ? 1 : 0;
+            c.dk_out[(size_t)slot * T + t] = dk;
+        }
+    }
+    V[k - lo] = Vk;
+    if (s.vec_spins) {
+        const int4 *src = reinterpret_cast<const int4 *>(sp);
+        int4 *dst = reinterpret_cast<int4 *>(gsp);
+        for (int i = 0; i < (s.N >> 4); ++i) dst[i] = src[i];
+    } else {
+        for (int i = 0; i < s.N; ++i) gsp[i] = sp[i];
+    }
+    if (!frozen)
+        for (int b = 0; b < nb; ++b) {
+            const uint32_t v = visits(V, glng, b, lnfq);
+            if (v != 0u) {
+                glng[b] = seqadd(glng[b], lnf, v);
+                gH[b] += v;
+            }
+        }
+    s.k[slot] = k;
+    s.step[slot] = st0 + (unsigned long long)T;
+    s.acc[slot] += nacc;
+    if (nex) atomicAdd(&s.status->n_exact, (unsigned long long)nex);
+    if (nmis) atomicAdd(&s.status->n_mismatch, (unsigned long long)nmis);
+}
+
+template <bool ISING, bool REPLAY, bool CHECK>
+__global__ void __launch_bounds__(256) k_move_thread(State s, MoveCfg c)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int slot = blockIdx.x * c.walkers_per_block + threadIdx.x;
+    if (threadIdx.x >= c.walkers_per_block || slot >= s.nw) return;
+    move_walker_thread<ISING, REPLAY, CHECK>(s, c, slot,
+                                             smem + (size_t)threadIdx.x * move_smem_per_thread_walker(s.N, s.W));
+}
+
 template <bool ISING, bool REPLAY, bool CHECK>
 __global__ void __launch_bounds__(512, 1) k_move(State s, MoveCfg c)
 {
@@ -461,7 +611,8 @@ __global__ void __launch_bounds__(512, 1) k_move(State s, MoveCfg c)
 }
 
 // Batched instances in one launch: CTA b serves walkers jobs[b].y .. jobs[b].y + jobs[b].z - 1 of
-// instance jobs[b].x; the model is chosen per CTA.
+// instance jobs[b].x & 0xffffff, one warp per walker, or one thread per walker when bit 24 of
+// jobs[b].x is set; the model and the layout are chosen per CTA.
 template <bool CHECK>
 __global__ void __launch_bounds__(512, 1) k_move_batch(const State *__restrict__ states,
                                                     const int4 *__restrict__ jobs, MoveCfg c)
@@ -469,8 +620,16 @@ __global__ void __launch_bounds__(512, 1) k_move_batch(const State *__restrict__
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int4 job = jobs[blockIdx.x];
+    const State s = states[job.x & 0xffffff];
+    if (job.x >> 24) { // one thread per walker
+        const int t = threadIdx.x;
+        if (t >= job.z) return;
+        unsigned char *base = smem + (size_t)t * move_smem_per_thread_walker(s.N, s.W);
+        if (s.model == 0) move_walker_thread<true, false, CHECK>(s, c, job.y + t, base);
+        else move_walker_thread<false, false, CHECK>(s, c, job.y + t, base);
+        return;
+    }
     if (wib >= job.z) return;
-    const State s = states[job.x];
     unsigned char *base = smem + (size_t)wib * move_smem_per_walker(s.N, s.W);
     if (s.model == 0) move_walker<true, false, CHECK>(s, c, job.y + wib, base, lane);
     else move_walker<false, false, CHECK>(s, c, job.y + wib, base, lane);
@@ -495,6 +654,31 @@ cudaError_t launch_move_batch(const State *states, const int4 *jobs, int njobs, 
 
 cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st)
 {
+    if (c.layout == 1) { // one thread per walker, c.walkers_per_block walkers (threads) per CTA
+        const int G = c.walkers_per_block;
+        const size_t smem = (size_t)G * move_smem_per_thread_walker(s.N, s.W);
+        const dim3 grid((s.nw + G - 1) / G), block((G + 31) & ~31);
+        const bool ising = s.model == 0;
+        cudaError_t e;
+#define REWL_LAUNCH_MOVE_T(I, R, C)                                                              \
+    do {                                                                                         \
+        e = cudaFuncSetAttribute(k_move_thread<I, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)smem);                                                     \
+        if (e != cudaSuccess) return e;                                                          \
+        k_move_thread<I, R, C><<<grid, block, smem, st>>>(s, c);                                 \
+    } while (0)
+        if (ising) {
+            if (c.words) REWL_LAUNCH_MOVE_T(true, true, false);
+            else if (c.check_all) REWL_LAUNCH_MOVE_T(true, false, true);
+            else REWL_LAUNCH_MOVE_T(true, false, false);
+        } else {
+            if (c.words) REWL_LAUNCH_MOVE_T(false, true, false);
+            else if (c.check_all) REWL_LAUNCH_MOVE_T(false, false, true);
+            else REWL_LAUNCH_MOVE_T(false, false, false);
+        }
+#undef REWL_LAUNCH_MOVE_T
+        return cudaGetLastError();
+    }
     const int G = c.walkers_per_block;
     const size_t smem = (size_t)G * move_smem_per_walker(s.N, s.W);
     const dim3 grid((s.nw + G - 1) / G), block(32 * G);
@@ -551,7 +735,7 @@ __global__ void k_init_prep(State s, long long prep_budget)
     int8_t *sp = s.spins + (size_t)slot * s.spin_stride; // cfg[slot] == slot at start
     const Lattice lat{s.L, N, s.magic};
     for (int c = 0; 4 * c < N; ++c) {
-        const u32x4 r = philox((uint32_t)c, 0u, (uint32_t)slot, (s.inst << 8) | TAG_INIT,
+        const u32x4 r = philox((uint32_t)c, 0u, (uint32_t)(s.slot0 + slot), (s.inst << 8) | TAG_INIT,
                                s.key0, s.key1);
         const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
         for (int j = 0; j < 4 && 4 * c + j < N; ++j)
@@ -574,7 +758,7 @@ __global__ void k_init_prep(State s, long long prep_budget)
         }
         const unsigned long long end = ps + budget;
         while (dist_to(k, lo, hi) > 0 && ps < end) {
-            const u32x4 r = philox((uint32_t)ps, (uint32_t)(ps >> 32), (uint32_t)slot,
+            const u32x4 r = philox((uint32_t)ps, (uint32_t)(ps >> 32), (uint32_t)(s.slot0 + slot),
                                    (s.inst << 8) | TAG_PREP, s.key0, s.key1);
             const int site = (int)mulhi(r.x, (uint32_t)N);
             int snew, dk;
@@ -733,24 +917,17 @@ cudaError_t launch_check(const State &s, double flatness, double lnf_final, cuda
 // lane 0 draws the partner permutation and the decisions (m is small), the swap itself
 // exchanges configuration indices and bins.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ void swap_pair(const State &s, const int pair)
+// Partner permutation of the exchange of pair (gw, gw+1) in round rd (global window index gw):
+// Fisher-Yates from Philox draws (i, rd, gw, swap tag), i = m-1 .. 1.  One warp; perm in shared
+// memory, valid after the call for every lane.
+__device__ __forceinline__ void exchange_perm(const State &s, int gw, long long rd, int *perm, int *draw)
 {
-    // one warp per window pair: the permutation's random draws and the m exchange decisions
-    // are lane-parallel (each decision touches its own two walker slots); only the
-    // Fisher-Yates swaps themselves run in order
-    if (s.status->done) return;
-    const long long rd = s.status->round;
-    const int w = 2 * pair + (int)(rd & 1);
-    if (w + 1 >= s.h) return;
-    const int lane = threadIdx.x & 31;
-    const int m = s.m, W = s.W;
-    __shared__ int perm[MAX_M];
-    __shared__ int draw[MAX_M];
+    const int lane = threadIdx.x & 31, m = s.m;
     const uint32_t tag = (s.inst << 8) | TAG_SWAP;
     for (int i = lane; i < m; i += 32) {
         perm[i] = i;
         if (i >= 1) {
-            const u32x4 r = philox((uint32_t)i, (uint32_t)rd, (uint32_t)w, tag, s.key0, s.key1);
+            const u32x4 r = philox((uint32_t)i, (uint32_t)rd, (uint32_t)gw, tag, s.key0, s.key1);
             draw[i] = (int)mulhi(r.x, (uint32_t)(i + 1));
         }
     }
@@ -763,6 +940,33 @@ __device__ __forceinline__ void swap_pair(const State &s, const int pair)
             perm[j] = t;
         }
     __syncwarp();
+}
+
+// Accept decision of Eq. (1) for partner pair i: ln P >= 0 or ln u < ln P, u from Philox
+// (m + i, rd, gw, swap tag).
+__device__ __forceinline__ bool exchange_accept(const State &s, int gw, long long rd, int i, double lnP)
+{
+    if (lnP >= 0.0) return true;
+    const u32x4 r = philox((uint32_t)(s.m + i), (uint32_t)rd, (uint32_t)gw, (s.inst << 8) | TAG_SWAP,
+                           s.key0, s.key1);
+    return lnu64(r.x) < lnP;
+}
+
+__device__ __forceinline__ void swap_pair(const State &s, const int pair)
+{
+    // one warp per window pair: the permutation's random draws and the m exchange decisions
+    // are lane-parallel (each decision touches its own two walker slots); only the
+    // Fisher-Yates swaps themselves run in order.  Pairs (w, w+1) with the global window
+    // index w0 + w of the parity of the round.
+    if (s.status->done) return;
+    const long long rd = s.status->round;
+    const int w = 2 * pair + (int)((rd + s.w0) & 1);
+    if (w + 1 >= s.h) return;
+    const int lane = threadIdx.x & 31;
+    const int m = s.m, W = s.W;
+    __shared__ int perm[MAX_M];
+    __shared__ int draw[MAX_M];
+    exchange_perm(s, s.w0 + w, rd, perm, draw);
     const int loA = s.lo[w], hiA = s.hi[w], loB = s.lo[w + 1], hiB = s.hi[w + 1];
     unsigned acc = 0;
     for (int i = lane; i < m; i += 32) {
@@ -772,13 +976,7 @@ __device__ __forceinline__ void swap_pair(const State &s, const int pair)
         const double *ga = s.lng + (size_t)a * W, *gb = s.lng + (size_t)b * W;
         const double lnP = __dadd_rn(__dsub_rn(ga[kx - loA], ga[ky - loA]),
                                      __dsub_rn(gb[ky - loB], gb[kx - loB]));
-        bool ok = lnP >= 0.0;
-        if (!ok) {
-            const u32x4 r = philox((uint32_t)(m + i), (uint32_t)rd, (uint32_t)w, tag, s.key0,
-                                   s.key1);
-            ok = lnu64(r.x) < lnP;
-        }
-        if (ok) {
+        if (exchange_accept(s, s.w0 + w, rd, i, lnP)) {
             const int t = s.cfg[a];
             s.cfg[a] = s.cfg[b];
             s.cfg[b] = t;
@@ -815,6 +1013,145 @@ cudaError_t launch_swap(const State &s, cudaStream_t st)
 {
     if (s.h < 2) return cudaSuccess;
     k_swap<<<(s.h + 1) / 2, 32, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Window-sharded runs: the exchange of the pair that straddles a shard boundary (Eq. 1).
+// Each shard runs its windows' rounds as usual; for the pair (gw, gw+1) across the boundary,
+// the shard of gw (side 1, its last window) and the shard of gw+1 (side 0, its first window)
+// trade, after the round, their walkers' bins, their half of ln P, and the lattices of the
+// accepted pairs.  Both sides draw the same permutation and the same random numbers, and add
+// the halves in the same order as the single-device exchange, so every decision is the same.
+// The round whose exchange this is has just ended: rd = round counter - 1.  One warp each.
+// ---------------------------------------------------------------------------------------
+struct BndPair {
+    int lw, gw;   // local window on this side, global index of the pair's lower window
+    long long rd; // round of the exchange
+    bool active;  // the pair exchanges in this round
+};
+
+__device__ __forceinline__ BndPair bnd_pair(const State &s, int side)
+{
+    BndPair b;
+    b.lw = side ? s.h - 1 : 0;
+    b.gw = side ? s.w0 + s.h - 1 : s.w0 - 1;
+    b.rd = s.status->round - 1;
+    b.active = b.rd >= 0 && ((b.rd - b.gw) & 1) == 0;
+    return b;
+}
+
+__global__ void k_bnd_bins(State s, int side, int *bins)
+{
+    const int lw = side ? s.h - 1 : 0;
+    for (int i = threadIdx.x; i < s.m; i += blockDim.x) bins[i] = s.k[lw * s.m + i];
+}
+
+__global__ void k_bnd_half(State s, int side, int plo, int phi, const int *pbins, double *half)
+{
+    __shared__ int perm[MAX_M];
+    __shared__ int draw[MAX_M];
+    const BndPair b = bnd_pair(s, side);
+    const int lane = threadIdx.x & 31, m = s.m;
+    if (!b.active) {
+        for (int i = lane; i < m; i += 32) half[i] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    exchange_perm(s, b.gw, b.rd, perm, draw);
+    const int lo = s.lo[b.lw], hi = s.hi[b.lw];
+    for (int i = lane; i < m; i += 32) {
+        double v = __longlong_as_double(0x7ff8000000000000LL); // NaN: the pair cannot exchange
+        if (side) { // own walker i of the lower window holds X
+            const int a = b.lw * m + i;
+            const int kx = s.k[a], ky = pbins[perm[i]];
+            const double *g = s.lng + (size_t)a * s.W;
+            if (kx >= plo && kx <= phi && ky >= lo && ky <= hi) v = __dsub_rn(g[kx - lo], g[ky - lo]);
+        } else { // own walker perm[i] of the upper window holds Y
+            const int a = b.lw * m + perm[i];
+            const int kx = pbins[i], ky = s.k[a];
+            const double *g = s.lng + (size_t)a * s.W;
+            if (kx >= lo && kx <= hi && ky >= plo && ky <= phi) v = __dsub_rn(g[ky - lo], g[kx - lo]);
+        }
+        half[i] = v;
+    }
+}
+
+__global__ void k_bnd_decide(State s, int side, const double *half, const double *phalf, uint8_t *acc,
+                             int8_t *lat_out)
+{
+    __shared__ int perm[MAX_M];
+    __shared__ int draw[MAX_M];
+    const BndPair b = bnd_pair(s, side);
+    const int lane = threadIdx.x & 31, m = s.m;
+    if (!b.active) {
+        for (int i = lane; i < m; i += 32) acc[i] = 0;
+        return;
+    }
+    exchange_perm(s, b.gw, b.rd, perm, draw);
+    unsigned na = 0;
+    for (int i = lane; i < m; i += 32) {
+        const double lower = side ? half[i] : phalf[i], upper = side ? phalf[i] : half[i];
+        const bool ok = lower == lower && upper == upper &&
+                        exchange_accept(s, b.gw, b.rd, i, __dadd_rn(lower, upper));
+        acc[i] = ok ? 1 : 0;
+        na += ok;
+    }
+    na = __reduce_add_sync(FULL, na);
+    __syncwarp();
+    // the lattices this side hands over (read before the partner's arrive)
+    for (int i = 0; i < m; ++i) {
+        if (!acc[i]) continue;
+        const int slot = b.lw * m + (side ? i : perm[i]);
+        const int8_t *src = s.spins + (size_t)s.cfg[slot] * s.spin_stride;
+        for (int j = lane; j < s.N; j += 32) lat_out[(size_t)i * s.N + j] = src[j];
+    }
+    if (side && lane == 0) { // the counters of pair gw live with its lower window
+        s.swap_att[b.lw] += (unsigned long long)m;
+        s.swap_acc[b.lw] += na;
+    }
+}
+
+__global__ void k_bnd_import(State s, int side, const int *pbins, const uint8_t *acc, const int8_t *plat)
+{
+    __shared__ int perm[MAX_M];
+    __shared__ int draw[MAX_M];
+    const BndPair b = bnd_pair(s, side);
+    const int lane = threadIdx.x & 31, m = s.m;
+    if (!b.active) return;
+    exchange_perm(s, b.gw, b.rd, perm, draw);
+    for (int i = 0; i < m; ++i) {
+        if (!acc[i]) continue;
+        const int slot = b.lw * m + (side ? i : perm[i]);
+        int8_t *dst = s.spins + (size_t)s.cfg[slot] * s.spin_stride;
+        for (int j = lane; j < s.N; j += 32) dst[j] = plat[(size_t)i * s.N + j];
+        if (lane == 0) s.k[slot] = side ? pbins[perm[i]] : pbins[i];
+    }
+}
+
+cudaError_t launch_bnd_bins(const State &s, int side, int *bins, cudaStream_t st)
+{
+    k_bnd_bins<<<1, 128, 0, st>>>(s, side, bins);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bnd_half(const State &s, int side, int plo, int phi, const int *pbins, double *half,
+                            cudaStream_t st)
+{
+    k_bnd_half<<<1, 32, 0, st>>>(s, side, plo, phi, pbins, half);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bnd_decide(const State &s, int side, const double *half, const double *phalf,
+                              uint8_t *acc, int8_t *lat_out, cudaStream_t st)
+{
+    k_bnd_decide<<<1, 32, 0, st>>>(s, side, half, phalf, acc, lat_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bnd_import(const State &s, int side, const int *pbins, const uint8_t *acc,
+                              const int8_t *plat, cudaStream_t st)
+{
+    k_bnd_import<<<1, 32, 0, st>>>(s, side, pbins, acc, plat);
     return cudaGetLastError();
 }
 

@@ -47,11 +47,13 @@ struct State {
     int production;           // rounds continue after every window finished
     DevStatus *status;
     uint32_t key0, key1, inst;
+    int w0, slot0;            // window-sharded run: global index of window 0 / walker slot 0
 };
 
 struct MoveCfg {
     int T;                  // attempts per walker in this launch
-    int walkers_per_block;  // warps per CTA
+    int walkers_per_block;  // walkers per CTA (warps, or threads with layout 1)
+    int layout;             // 0: one warp per walker, 1: one thread per walker
     int check_all;
     double eps_l;
     const uint32_t *words;  // replay: [nw][T][3], else nullptr (Philox)
@@ -68,6 +70,12 @@ __host__ __device__ inline size_t move_smem_per_walker(int N, int W)
 {
     return (size_t)((N + 15) & ~15) + (size_t)((W + 3) & ~3) * 8u + (size_t)visw(W) * 4u +
            (size_t)((N + 7) & ~7) * 2u;
+}
+// Shared memory of one walker of the thread-per-walker layout: lattice (16-byte padded) and the
+// int64 ln g shadow over the window (padded to 2 bins, 16 bytes).
+__host__ __device__ inline size_t move_smem_per_thread_walker(int N, int W)
+{
+    return (size_t)((N + 15) & ~15) + (size_t)((W + 1) & ~1) * 8u;
 }
 cudaError_t launch_move(const State &s, const MoveCfg &c, cudaStream_t st);
 // Batched instances: states/jobs/tables are device arrays (see the kernels).
@@ -89,6 +97,15 @@ cudaError_t launch_stitch(const State &s, const double *mean, double de, int ste
                           double target, double *out /*B+1*/, int *joins /*h-1*/,
                           int *ok /*1*/, int B, cudaStream_t st);
 
+// window-sharded runs: the exchange of the pair across a shard boundary (Eq. 1), in four steps
+// (side 1: this shard holds the pair's lower window, its last; side 0: the upper, its first)
+cudaError_t launch_bnd_bins(const State &s, int side, int *bins, cudaStream_t st);
+cudaError_t launch_bnd_half(const State &s, int side, int plo, int phi, const int *pbins,
+                            double *half, cudaStream_t st);
+cudaError_t launch_bnd_decide(const State &s, int side, const double *half, const double *phalf,
+                              uint8_t *acc, int8_t *lat_out, cudaStream_t st);
+cudaError_t launch_bnd_import(const State &s, int side, const int *pbins, const uint8_t *acc,
+                              const int8_t *plat, cudaStream_t st);
 cudaError_t launch_loo_mean(const State &s, int j, double *out /*[h][W]*/, cudaStream_t st);
 cudaError_t launch_jack(const double *theta /*[m][B+1]*/, int m, int B, double *err, cudaStream_t st);
 cudaError_t launch_thermo(const double *lng, int model, int L, const double *T, int nT, double *U,

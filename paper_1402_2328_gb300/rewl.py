@@ -70,12 +70,18 @@ def lib():
             "rewl_lnu_eps": ([], D),
             "rewl_seqadd": ([P, P, P, P, I, P], I),
             "rewl_windows_balanced": ([P, I, I, D, P], I),
+            "rewl_windows_equal": ([I, I, D, P], I),
             "rewl_thermo": ([P, I, I, P, I, P, P, P], I),
             "rewl_jackknife": ([P, P, I, I], I),
             "rewl_get_hist_em": ([P, P, C.c_size_t], I),
             "rewl_stitch_em": ([P, P, C.c_size_t, P], I),
             "rewl_join_em": ([P, I, I, I, I, P, D, D, D, P, P, P], I),
             "rewl_balanced_from_prerun": ([P, I, D, P], I),
+            "rewl_set_shard": ([P, P, I, I], I),
+            "rewl_boundary_bins": ([P, I, P], I),
+            "rewl_boundary_half": ([P, I, P, P], I),
+            "rewl_boundary_decide": ([P, I, P, P, P, P], I),
+            "rewl_boundary_import": ([P, I, P, P, P], I),
             "rewl_balanced_scaled": ([P, I, I, D, P], I),
             "rewl_mlp_forward": ([P, P, P, I, P], I),
             "rewl_mlp_workspace_floats": ([I], I),
@@ -224,6 +230,27 @@ class REWL:
     def set_stream(self, stream=None):
         _check(self._lib.rewl_set_stream(self._h, _stream_ptr(stream)), self._h)
 
+    def set_shard(self, lo, hi, w_begin: int):
+        """This handle runs windows w_begin .. w_begin + windows - 1 of the global layout."""
+        a = np.ascontiguousarray(np.concatenate([lo, hi]), np.int32)
+        _check(self._lib.rewl_set_shard(self._h, _ptr(a), len(lo), int(w_begin)), self._h)
+        self._update_dims()
+
+    def boundary_bins(self, side: int, bins):
+        _check(self._lib.rewl_boundary_bins(self._h, int(side), _ptr(bins)), self._h)
+
+    def boundary_half(self, side: int, partner_bins, half):
+        _check(self._lib.rewl_boundary_half(self._h, int(side), _ptr(partner_bins), _ptr(half)),
+               self._h)
+
+    def boundary_decide(self, side: int, half, partner_half, accepted, lattices):
+        _check(self._lib.rewl_boundary_decide(self._h, int(side), _ptr(half), _ptr(partner_half),
+                                              _ptr(accepted), _ptr(lattices)), self._h)
+
+    def boundary_import(self, side: int, partner_bins, accepted, partner_lattices):
+        _check(self._lib.rewl_boundary_import(self._h, int(side), _ptr(partner_bins), _ptr(accepted),
+                                              _ptr(partner_lattices)), self._h)
+
     def balanced_windows(self, h: int, overlap: float = 0.75):
         """Windows balanced by this (pre-)run's first-iteration times (Fig. 1b)."""
         a = np.zeros(2 * h, np.int32)
@@ -366,11 +393,21 @@ class REWLBatch:
                                              C.byref(st)))
         return STATUS[st.value]
 
+    TUNE_WALKERS = (2, 4, 8, 16)
+    TUNE_SITES = (0, 400, 1024, 1600)
+    TUNE_GRAPH = (8, 32, 128)
+
     def autotune(self, rounds: int = 2):
-        best = C.c_int(0)
-        ms = (C.c_double * 4)()
-        self._check(self._lib.rewl_batch_autotune(self._h, int(rounds), C.byref(best), ms))
-        return best.value, dict(zip((2, 4, 8, 16), list(ms)))
+        """Choose warps per CTA x thread-per-walker site limit, then rounds per graph replay;
+        returns (choice, {candidate: ms per round})."""
+        best = (C.c_int * 3)()
+        ms = (C.c_double * 19)()
+        self._check(self._lib.rewl_batch_autotune(self._h, int(rounds), best, ms))
+        keys = [f"w{w}_t{t}" for t in self.TUNE_SITES for w in self.TUNE_WALKERS]
+        keys += [f"graph{g}" for g in self.TUNE_GRAPH]
+        choice = dict(walkers_per_block=best[0], thread_layout_max_sites=best[1],
+                      graph_rounds=best[2])
+        return choice, dict(zip(keys, list(ms)))
 
     def instance(self, i: int) -> REWL:
         h = C.c_void_p()
@@ -378,10 +415,11 @@ class REWLBatch:
         return REWL._view(h)
 
     def info(self):
-        out = np.zeros(4, np.int32)
+        out = np.zeros(6, np.int32)
         self._check(self._lib.rewl_batch_info(self._h, _ptr(out)))
         return dict(instances=int(out[0]), walkers=int(out[1]), ctas=int(out[2]),
-                    warps_per_cta=int(out[3]))
+                    warps_per_cta=int(out[3]), thread_layout_max_sites=int(out[4]),
+                    graph_rounds=int(out[5]))
 
     def kernel_time(self, reset: bool = True):
         ms, n = C.c_double(), C.c_longlong()
@@ -424,6 +462,18 @@ def join_em(S, lo, hi, B: int, out, de: float = 4.0, dq: float = 2.0, norm_targe
     _check(lib().rewl_join_em(_ptr(S), int(h), int(W), int(B), int(N1), _ptr(lohi), float(de),
                               float(dq), tgt, _ptr(out), _ptr(joins), _stream_ptr(stream)))
     return joins[: h - 1]
+
+
+def num_bins(model: int, L: int) -> int:
+    """B: the bins are 0..B (Ising B = N, Potts B = 2N)."""
+    return L * L if model == 0 else 2 * L * L
+
+
+def windows_layout(B: int, h: int, overlap: float = 0.75):
+    """The equal-size window layout of Fig. 1a (the one rewl_create uses): (lo, hi)."""
+    a = np.zeros(2 * h, np.int32)
+    _check(lib().rewl_windows_equal(int(B), int(h), float(overlap), _ptr(a)))
+    return a[:h].copy(), a[h:].copy()
 
 
 def windows_balanced(cost, h: int, overlap: float = 0.75):

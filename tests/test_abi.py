@@ -98,3 +98,17 @@ def test_create_refuses_lnf_final_below_the_shadow_resolution(built):
     rc = lib.rewl_create(ctypes.byref(h), 0, 8, 2, 0.75, 1, 2.0 ** -33, 0.8)
     assert rc == -1 and not h.value
     assert b"invalid argument" in lib.rewl_last_error(None)
+
+
+def test_equal_windows_match_the_oracle(built):
+    """The library's Fig. 1a layout (a host call, no device needed) equals the oracle's."""
+    import numpy as np
+    import oracle as O
+    import paper_1402_2328_gb300.rewl as R
+    for B, h, o in [(64, 4, 0.75), (4096, 32, 0.75), (12800, 64, 0.75), (3200, 64, 0.75),
+                    (1000, 7, 0.5), (257, 3, 0.6)]:
+        lo, hi = R.windows_layout(B, h, o)
+        olo, ohi = O.windows(B, h, o)
+        assert np.array_equal(lo, olo) and np.array_equal(hi, ohi), (B, h, o)
+    with pytest.raises(R.REWLError):
+        R.windows_layout(16, 40, 0.75)

@@ -57,14 +57,14 @@ def _solo(R, d, interval, rounds):
     return st
 
 
-@pytest.mark.parametrize("wpb", [0, 1, 16])
-def test_small_batch_equals_solo_and_oracle(R, wpb):
+@pytest.mark.parametrize("wpb,tsites", [(0, 0), (1, 0), (16, 0), (4, 100), (1, 256)])
+def test_small_batch_equals_solo_and_oracle(R, wpb, tsites):
     descs = [dict(model=0, L=8, windows=4, walkers=2, lnf_final=1e-4, seed=11, instance=0),
              dict(model=3, L=6, windows=3, walkers=3, lnf_final=1e-4, seed=12, instance=1),
              dict(model=0, L=16, windows=8, walkers=4, lnf_final=1e-4, seed=13, instance=2),
              dict(model=10, L=12, windows=8, walkers=2, lnf_final=1e-4, seed=14, instance=3),
              dict(model=0, L=5, windows=1, walkers=1, lnf_final=1e-4, seed=15, instance=4)]
-    b = R.REWLBatch(descs, interval=700, walkers_per_block=wpb)
+    b = R.REWLBatch(descs, interval=700, walkers_per_block=wpb, thread_layout_max_sites=tsites)
     b.init()
     b.run(max_rounds=40)
     for i, d in enumerate(descs):
@@ -121,20 +121,25 @@ def test_config4_batch_autotuned_equals_solo(R):
     descs = config4_descs()
     b = R.REWLBatch(descs, interval=10_000)
     b.init()
-    best, ms = b.autotune(rounds=1)  # 4 trial rounds of the simulation itself
-    assert best in (2, 4, 8, 16) and all(v > 0 for v in ms.values())
+    best, ms = b.autotune(rounds=1)  # trial rounds of the simulation itself
+    assert best["walkers_per_block"] in (2, 4, 8, 16) and best["graph_rounds"] in (8, 32, 128)
+    assert best["thread_layout_max_sites"] in (0, 400, 1024, 1600)
+    assert all(v > 0 for v in ms.values())  # every site limit applies to some instance here
     b.run(max_rounds=1)
     info = b.info()
     assert info["instances"] == 24 and info["walkers"] == 6720
+    assert info["thread_layout_max_sites"] == best["thread_layout_max_sites"]
+    rounds = int(b.instance(0).get_state("round")[0])
+    assert rounds == 16 + 8 + 32 + 128 + 1
     for i in (0, 2, 3, 7, 12, 17, 23):
-        _same(b.instance(i).state(), _solo(R, descs[i], 10_000, 5))
-    # the first instances of each model against the oracle, five rounds (the same rounds:
-    # the autotuner's trial rounds are ordinary rounds)
+        _same(b.instance(i).state(), _solo(R, descs[i], 10_000, rounds))
+    # the first instances of each model against the oracle, the same rounds (the autotuner's
+    # trial rounds are ordinary rounds, whatever layout ran them)
     for i in (0, 3):
         d = descs[i]
         o = O.REWL(d["model"], d["L"], d["windows"], 0.75, d["walkers"], d["lnf_final"], 0.8,
                    seed=d["seed"], instance=d["instance"], interval=10_000)
         assert o.init() == 0
-        o.run(5)
+        o.run(rounds)
         _same(b.instance(i).state(), o.state())
     b.close()
