@@ -453,8 +453,27 @@ def run_warm(args):
     t_fit = time.perf_counter() - t1
     lng_pred = WM.predict_lng(P, args.warm_model, args.warm_L)
 
+    # run-time balanced windows of the target lattice itself (Fig. 1b): a pre-run with equal
+    # windows until every window finished its first iteration, then the balanced layout
+    bal = None
+    if any(v.partition("@")[0].endswith("_bal") for v in args.warm_variants.split(",")):
+        pre = R.REWL(args.warm_model, args.warm_L, args.warm_windows, 0.75, args.warm_walkers,
+                     args.warm_lnf_final, 0.8, seed=seed_for(5, 900), interval=10_000)
+        pre.init()
+        tp = time.perf_counter()
+        while time.perf_counter() - tp < args.max_seconds:
+            pre.run(max_rounds=500)
+            if np.all(pre.get_state("first_iter_round") > 0):
+                break
+        t1 = pre.get_state("first_iter_round")
+        bal = dict(seconds=time.perf_counter() - tp, rounds=int(pre.get_state("round")[0]),
+                   complete=bool(np.all(t1 > 0)))
+        bal["lo"], bal["hi"] = pre.balanced_windows(args.warm_windows, 0.75)
+        pre.close()
+
     def target(seed, variant):
-        # variant: kind[@ln f0], kind in warm (learned windows), warm_eq, cold, cold_lw
+        # variant: kind[@ln f0], kind in warm (learned windows), warm_eq, cold, cold_lw and
+        # cold_bal / warm_bal (windows balanced by the pre-run on the target lattice)
         kind, _, lnf0 = variant.partition("@")
         if kind.startswith("warm"):
             r = WM.warm_handle(args.warm_model, args.warm_L, args.warm_windows, args.warm_walkers,
@@ -465,6 +484,8 @@ def run_warm(args):
                        args.warm_lnf_final, 0.8, seed=seed, interval=10_000)
         if kind in ("warm", "cold_lw"):
             r.set_windows(lw_lo, lw_hi)
+        if kind.endswith("_bal"):
+            r.set_windows(bal["lo"], bal["hi"])
         ts = time.perf_counter()
         status = r.run(max_seconds=args.max_seconds)
         dt = time.perf_counter() - ts
@@ -472,6 +493,11 @@ def run_warm(args):
         out = dict(status=status, seconds=dt, rounds=s_r["rounds"], attempts=s_r["attempts"],
                    windows_finished=s_r["windows_finished"], max_lnf=s_r["max_lnf"])
         lng = r.stitch(0)[0] if status == "done" else None
+        if status == "done" and r.m >= 2:
+            err = r.jackknife(0)
+            ok = np.isfinite(err) & np.isfinite(lng)
+            out["jackknife_max"] = float(err[ok].max())
+            out["jackknife_rms"] = float(np.sqrt(np.mean(err[ok] ** 2)))
         r.close()
         return out, lng
 
@@ -547,9 +573,17 @@ def run_warm(args):
         "fit_seconds": t_fit, "fit_loss": hist[-1][1],
         "runs": results, "over_seeds": summary,
         "learned_windows": {"lo": lw_lo.tolist(), "hi": lw_hi.tolist()},
+        "balanced_prerun": ({k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in bal.items()}
+                            if bal else None),
         "speedup_time": (cold["seconds"] / warm["seconds"])
         if cold and warm and warm["status"] == "done" and cold["status"] == "done" else None,
         "max_abs_dlng_warm_vs_cold": maxdiff(lng_warm, lng_cold),
+        # every pair of finished variants of the first seed, and of two seeds of one variant
+        "pairwise_max_abs_dlng": {
+            **{f"{a}|{b}": maxdiff(lngs[a], lngs[b]) for a in lngs for b in lngs
+               if a < b and lngs[a] is not None and lngs[b] is not None},
+            **{f"{k}|seed0-seed1": maxdiff(lst[0][1], lst[1][1]) for k, lst in per_seed.items()
+               if len(lst) > 1 and lst[0][1] is not None and lst[1][1] is not None}},
         "max_abs_dlng_prediction_vs_cold": maxdiff(pred_n, lng_cold),
     }}
 

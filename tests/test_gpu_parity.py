@@ -407,13 +407,14 @@ def test_smallest_and_largest_lattices_bit_exact(model, L, h, m):
 @pytest.mark.parametrize("check", [0, 1])
 @pytest.mark.parametrize("model,L,h,m,rounds,interval,sched", [
     (0, 8, 4, 8, 60, 1000, 0), (3, 6, 3, 16, 60, 700, 1), (0, 16, 8, 40, 25, 2000, 0),
-    (10, 12, 8, 33, 25, 1500, 1), (0, 5, 2, 3, 80, 333, 0), (0, 32, 16, 70, 6, 3000, 1)])
+    (10, 12, 8, 33, 25, 1500, 1), (0, 5, 2, 3, 80, 333, 0), (0, 32, 16, 70, 10, 3000, 1)])
 def test_thread_layout_rounds_bit_exact(model, L, h, m, rounds, interval, sched, check):
     """The thread-per-walker move kernel (layout 1) against the oracle, round by round."""
     g, o = _pair(model, L, h, m, seed=13 + L, interval=interval, check_all=check, layout=1,
                  schedule=sched)
     g.init()
     assert o.init() == 0
+    assert rounds > 8
     for chunk in (1, 7, rounds - 8):
         g.run(max_rounds=chunk)
         o.run(chunk)
