@@ -200,7 +200,6 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
     // interval-constant part of the float32 screening margin (ln units)
     const float Mbase = (float)(c.eps_l + 2.0 * shadow_error(mx, T, lnf, frozen) * 0x1p-32) + 0x1p-21f;
     const float lnf_f = frozen ? 0.0f : (float)lnf;
-    const bool late = 33.0f * lnf_f <= 0x1p-12f; // the batch-start cache decides (see below)
     __syncwarp();
 
     const unsigned long long st0 = s.step[slot];
@@ -308,52 +307,6 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
         int myx = 16;      // lane j: cache offset of the bin after step j
         bool myun = false; // lane j: step j unsure in float32
         bool mysa = false, mysr = false; // CHECK: float32 verdict of step j (sure accept / reject)
-        if (late) {
-            // Late stage (33 ln f <= 2^-12, or a frozen window): the visits of the batch's
-            // earlier steps change any ln g(k) - ln g(k') by at most 31 ln f, so every step is
-            // decided on the batch-start cache with the margin widened by 33 ln f.  Lane l
-            // tabulates, 8 steps at a time, where a walker standing in cache bin l is after the
-            // step (bits 0-4; bit 5: unsure or target outside the cache; CHECK: bit 6 sure
-            // accept, bit 7 sure reject).  The walk is then one shuffle per step, and the next
-            // 8 steps' table is computed in the shuffles' shadow.
-            const float Mf = M + 33.0f * lnf_f;
-            auto table = [&](int j) -> int {
-                const int dkj = __shfl_sync(FULL, dk, j);
-                const float thj = __shfl_sync(FULL, thr, j);
-                const int tg = lane + dkj;
-                const float Lt = __shfl_sync(FULL, Lw, tg & 31);
-                const float e = (Lw - Lt) - thj;
-                const bool un = (unsigned)tg >= 32u ||
-                                (CHECK ? (thj != INFINITY && Lt != INFINITY) : !(fabsf(e) > Mf));
-                int f = ((e > Mf) ? tg : lane) & 31;
-                f |= un ? 32 : 0;
-                if (CHECK) f |= (e > Mf ? 64 : 0) | (e < -Mf ? 128 : 0);
-                return f;
-            };
-            int f[8], g[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) f[q] = table(q);
-            int x = 16, rec = 16, seen = 0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    x = __shfl_sync(FULL, f[q], x); // the source lane is x mod 32
-                    seen |= x;
-                    if (lane == 8 * c + q) rec = x;
-                    if (c < 3) g[q] = table(8 * (c + 1) + q);
-                }
-                if (c == 3 || 8 * (c + 1) >= J || (seen & 32) != 0) break;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) f[q] = g[q];
-            }
-            myx = rec & 31;
-            myun = (rec & 32) != 0;
-            if (CHECK) {
-                mysa = (rec & 64) != 0;
-                mysr = (rec & 128) != 0;
-            }
-        } else {
         int xk = 16;       // cache offset of the current bin
         float Lk = 0.0f;   // running value of the current bin (the cache holds it only once left)
 #pragma unroll
@@ -408,7 +361,6 @@ __device__ __forceinline__ void move_walker(const State &s, const MoveCfg &c, co
                 }
             }
             Lk = (m1 ? L1 : Lc1) + lnf_f;
-        }
         }
         // bin before step j; a target outside the cache makes step j unsure as well
         const int xup = __shfl_up_sync(FULL, myx, 1);
