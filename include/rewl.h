@@ -122,6 +122,22 @@ int rewl_set_windows(rewl_t r, const int *lo_hi, int h);
 int rewl_windows_equal(int B, int h, double overlap, int *lo_hi);
 
 /*
+ * rewl_windows_late_balanced -- windows balanced by the cost of the later WL iterations (Fig. 1b
+ * names the first iteration; the footnote to it allows adapting the layout as the run
+ * proceeds).  lo_hi (host, 2h ints) is the layout of a pre-run and rounds_per_iter[w] the
+ * rounds its window w took per iteration over some later iterations (<= 0: not measured,
+ * counted as the slowest).  Per window a = rounds per iteration / width^2 (a later iteration's
+ * time grows about with the square of the width); every bin costs sqrt(a), averaged over the
+ * windows covering it; lo_hi_out (2*h_new ints) = rewl_windows_balanced of that cost, so the
+ * new windows have about equal a * width^2.  Host only.  INVALID_ARG for a bad layout or no
+ * measured window.  (First-iteration balancing over-widens windows whose first iteration is
+ * cheap: for q = 10 Potts L = 80 it left the high-energy windows 2-4 times wider than equal
+ * ones and slower than before.)
+ */
+int rewl_windows_late_balanced(const int *lo_hi, int h, const double *rounds_per_iter, int B,
+                               int h_new, double overlap, int *lo_hi_out);
+
+/*
  * rewl_windows_balanced -- run-time balanced windows (Fig. 1b).  host cost[B+1] >= 0 is the
  * expected first-iteration work per bin; the h windows are the equal-size layout with overlap
  * `overlap` placed in the coordinate u(b) = (cumulative cost up to b) / (total cost), so every

@@ -691,6 +691,45 @@ int rewl_windows_equal(int B, int h, double overlap, int *lo_hi)
     return REWL_OK;
 }
 
+int rewl_windows_late_balanced(const int *lo_hi, int h, const double *rounds_per_iter, int B,
+                               int h_new, double overlap, int *lo_hi_out)
+{
+    if (!lo_hi || !rounds_per_iter || !lo_hi_out || h < 1 || B < 1 || h_new < 1) {
+        g_err = "rewl_windows_late_balanced: invalid argument";
+        return REWL_ERR_INVALID_ARG;
+    }
+    // per window a = (rounds per late iteration) / width^2; a bin costs sqrt(a) (the mean over
+    // the windows covering it), so windows of equal summed cost have equal a * width^2
+    std::vector<double> a(h, -1.0);
+    double amax = 0.0;
+    for (int w = 0; w < h; ++w) {
+        const int lo = lo_hi[w], hi = lo_hi[h + w];
+        if (lo < 0 || hi > B || hi < lo) {
+            g_err = "rewl_windows_late_balanced: window outside [0, B]";
+            return REWL_ERR_INVALID_ARG;
+        }
+        const double t = rounds_per_iter[w], wd = (double)(hi - lo + 1);
+        if (t > 0.0 && std::isfinite(t)) {
+            a[w] = t / (wd * wd);
+            amax = std::max(amax, a[w]);
+        }
+    }
+    if (!(amax > 0.0)) {
+        g_err = "rewl_windows_late_balanced: no window has a measured iteration time";
+        return REWL_ERR_INVALID_ARG;
+    }
+    std::vector<double> cost(B + 1, 0.0), cnt(B + 1, 0.0);
+    for (int w = 0; w < h; ++w) {
+        const double c = std::sqrt(a[w] > 0.0 ? a[w] : amax); // unmeasured: as the slowest
+        for (int b = lo_hi[w]; b <= lo_hi[h + w]; ++b) {
+            cost[b] += c;
+            cnt[b] += 1.0;
+        }
+    }
+    for (int b = 0; b <= B; ++b) cost[b] = cnt[b] > 0.0 ? cost[b] / cnt[b] : std::sqrt(amax);
+    return rewl_windows_balanced(cost.data(), B, h_new, overlap, lo_hi_out);
+}
+
 int rewl_windows_balanced(const double *cost, int B, int h, double overlap, int *lo_hi)
 {
     if (!cost || !lo_hi || B < 1 || h < 1 || !(overlap >= 0.0 && overlap < 1.0)) {

@@ -71,6 +71,7 @@ def lib():
             "rewl_seqadd": ([P, P, P, P, I, P], I),
             "rewl_windows_balanced": ([P, I, I, D, P], I),
             "rewl_windows_equal": ([I, I, D, P], I),
+            "rewl_windows_late_balanced": ([P, I, P, I, I, D, P], I),
             "rewl_thermo": ([P, I, I, P, I, P, P, P], I),
             "rewl_jackknife": ([P, P, I, I], I),
             "rewl_get_hist_em": ([P, P, C.c_size_t], I),
@@ -474,6 +475,16 @@ def windows_layout(B: int, h: int, overlap: float = 0.75):
     a = np.zeros(2 * h, np.int32)
     _check(lib().rewl_windows_equal(int(B), int(h), float(overlap), _ptr(a)))
     return a[:h].copy(), a[h:].copy()
+
+
+def windows_late_balanced(lo, hi, rounds_per_iter, B: int, h_new: int, overlap: float = 0.75):
+    """Windows with about equal (rounds per later iteration / width^2) x width^2 (host call)."""
+    lh = np.ascontiguousarray(np.concatenate([lo, hi]), np.int32)
+    t = np.ascontiguousarray(rounds_per_iter, np.float64)
+    out = np.zeros(2 * h_new, np.int32)
+    _check(lib().rewl_windows_late_balanced(_ptr(lh), len(lo), _ptr(t), int(B), int(h_new),
+                                            float(overlap), _ptr(out)))
+    return out[:h_new].copy(), out[h_new:].copy()
 
 
 def windows_balanced(cost, h: int, overlap: float = 0.75):

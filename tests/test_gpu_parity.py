@@ -431,3 +431,25 @@ def test_thread_layout_to_completion_bit_exact():
     o.run(10 ** 7)
     _same(g.state(), o.state())
     g.close()
+
+
+def test_late_balanced_windows_pipeline():
+    """Pre-run to the 4th iteration of every window, windows balanced by the 2nd-4th
+    iterations' cost (paper_1402_2328_gb300.balance); the layout runs bit-exactly against the
+    oracle with the same windows."""
+    import paper_1402_2328_gb300.rewl as R
+    from paper_1402_2328_gb300 import balance as BL
+    pre = R.REWL(0, 16, 8, 0.75, 2, 1e-4, 0.8, seed=15, interval=2000)
+    lo, hi, info = BL.late_balanced_windows(pre, 8, it_from=2, it_to=4, chunk=16, max_seconds=120)
+    assert info["complete"] and lo[0] == 0 and hi[-1] == 256
+    assert np.all(lo[1:] <= hi[:-1]) and np.all(np.diff(lo) > 0)
+    pre.close()
+    g = R.REWL(0, 16, 8, 0.75, 2, 1e-4, 0.8, seed=16, interval=900)
+    g.set_windows(lo, hi)
+    o = O.REWL(0, 16, 8, 0.75, 2, 1e-4, 0.8, seed=16, interval=900, lo_hi=(lo, hi))
+    g.init()
+    assert o.init() == 0
+    g.run(max_rounds=20)
+    o.run(20)
+    _same(g.state(), o.state())
+    g.close()

@@ -37,3 +37,26 @@ def test_windows_follow_the_cost(R):
 def test_rejects_bad_cost(R):
     with pytest.raises(R.REWLError):
         R.windows_balanced(np.array([1.0, -1.0, 1.0]), 1)
+
+
+def test_late_balanced_layout_properties():
+    """Windows balanced by later-iteration cost (host call): a valid layout; equal cost keeps
+    equal-size windows; a window that takes 16x longer per iteration becomes ~4x narrower."""
+    import numpy as np
+    import paper_1402_2328_gb300.rewl as R
+    B, h = 4096, 16
+    lo, hi = R.windows_layout(B, h, 0.75)
+    for per in (np.full(h, 1000.0), np.r_[16000.0, np.full(h - 1, 1000.0)],
+                np.r_[np.full(h - 1, 1000.0), -1.0]):
+        nlo, nhi = R.windows_late_balanced(lo, hi, per, B, h, 0.75)
+        assert nlo[0] == 0 and nhi[-1] == B
+        assert np.all(np.diff(nlo) > 0) and np.all(np.diff(nhi) > 0)
+        assert np.all(nlo[1:] <= nhi[:-1])           # neighbours overlap
+    w_eq = (hi - lo + 1).astype(float)
+    nlo, nhi = R.windows_late_balanced(lo, hi, np.full(h, 1000.0), B, h, 0.75)
+    assert np.max(np.abs((nhi - nlo + 1) - w_eq)) <= 2
+    nlo, nhi = R.windows_late_balanced(lo, hi, np.r_[16000.0, np.full(h - 1, 1000.0)], B, h, 0.75)
+    ratio = (nhi[0] - nlo[0] + 1) / w_eq[0]
+    assert 0.15 < ratio < 0.45, ratio
+    with pytest.raises(R.REWLError):
+        R.windows_late_balanced(lo, hi, np.full(h, -1.0), B, h, 0.75)
