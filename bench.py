@@ -471,9 +471,22 @@ def run_warm(args):
         bal["lo"], bal["hi"] = pre.balanced_windows(args.warm_windows, 0.75)
         pre.close()
 
+    # windows balanced by the cost of later iterations (rounds per iteration over iterations
+    # 3..6 of an equal-window pre-run on the target lattice)
+    late = None
+    if any(v.partition("@")[0].endswith("_late") for v in args.warm_variants.split(",")):
+        from paper_1402_2328_gb300 import balance as BL
+        pre = R.REWL(args.warm_model, args.warm_L, args.warm_windows, 0.75, args.warm_walkers,
+                     args.warm_lnf_final, 0.8, seed=seed_for(5, 900), interval=10_000)
+        llo, lhi, late = BL.late_balanced_windows(pre, args.warm_windows, 3, 6,
+                                                  max_seconds=args.max_seconds)
+        late.update(lo=llo, hi=lhi)
+        pre.close()
+
     def target(seed, variant):
-        # variant: kind[@ln f0], kind in warm (learned windows), warm_eq, cold, cold_lw and
-        # cold_bal / warm_bal (windows balanced by the pre-run on the target lattice)
+        # variant: kind[@ln f0], kind in warm (learned windows), warm_eq, cold, cold_lw,
+        # cold_bal / warm_bal (windows balanced by the pre-run's first iterations) and
+        # cold_late / warm_late (balanced by its later iterations)
         kind, _, lnf0 = variant.partition("@")
         if kind.startswith("warm"):
             r = WM.warm_handle(args.warm_model, args.warm_L, args.warm_windows, args.warm_walkers,
@@ -486,6 +499,8 @@ def run_warm(args):
             r.set_windows(lw_lo, lw_hi)
         if kind.endswith("_bal"):
             r.set_windows(bal["lo"], bal["hi"])
+        if kind.endswith("_late"):
+            r.set_windows(late["lo"], late["hi"])
         ts = time.perf_counter()
         status = r.run(max_seconds=args.max_seconds)
         dt = time.perf_counter() - ts
@@ -575,6 +590,8 @@ def run_warm(args):
         "learned_windows": {"lo": lw_lo.tolist(), "hi": lw_hi.tolist()},
         "balanced_prerun": ({k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in bal.items()}
                             if bal else None),
+        "late_balanced_prerun": ({k: (v.tolist() if hasattr(v, "tolist") else v)
+                                  for k, v in late.items()} if late else None),
         "speedup_time": (cold["seconds"] / warm["seconds"])
         if cold and warm and warm["status"] == "done" and cold["status"] == "done" else None,
         "max_abs_dlng_warm_vs_cold": maxdiff(lng_warm, lng_cold),
@@ -885,8 +902,9 @@ def main():
     ap.add_argument("--speedup-interval", type=int, default=10_000)
     ap.add_argument("--warm-seeds", type=int, default=1, help="target runs per variant")
     ap.add_argument("--warm-variants", default="cold,warm",
-                    help="comma list of cold | warm | cold_lw | warm_eq (lw: learned windows), "
-                         "each optionally @ln_f0, e.g. warm_eq@0.01")
+                    help="comma list of cold | warm | cold_lw | warm_eq (lw: learned windows) | "
+                         "cold_bal | warm_bal (first-iteration balanced) | cold_late | warm_late "
+                         "(later-iteration balanced), each optionally @ln_f0, e.g. warm_eq@0.01")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
