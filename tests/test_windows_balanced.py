@@ -60,3 +60,41 @@ def test_late_balanced_layout_properties():
     assert 0.15 < ratio < 0.45, ratio
     with pytest.raises(R.REWLError):
         R.windows_late_balanced(lo, hi, np.full(h, -1.0), B, h, 0.75)
+
+
+class _FakePre:
+    """A pre-run whose window w completes an iteration every (w + 1) * 10 rounds."""
+    h, B = 4, 64
+
+    def __init__(self):
+        self.rd = 0
+        import numpy as np
+        import paper_1402_2328_gb300.rewl as R
+        self.lo, self.hi = R.windows_layout(self.B, self.h, 0.75)
+        self.np = np
+
+    def run(self, max_rounds=-1, **kw):
+        self.rd += max(0, max_rounds)
+        return "budget"
+
+    def get_state(self, f):
+        np = self.np
+        if f == "iter":
+            return np.array([self.rd // (10 * (w + 1)) for w in range(self.h)], np.int32)
+        if f == "round":
+            return np.array([self.rd], np.int64)
+        return {"lo": self.lo, "hi": self.hi}[f]
+
+
+def test_late_balance_helper_reads_iteration_times():
+    """balance.late_balanced_windows: iteration completion rounds polled between chunks give
+    the rounds per iteration of each window; the slowest window comes out narrowest."""
+    from paper_1402_2328_gb300 import balance as BL
+    pre = _FakePre()
+    lo, hi, info = BL.late_balanced_windows(pre, 4, it_from=2, it_to=4, chunk=5, max_seconds=30)
+    assert info["complete"]
+    assert info["rounds_per_iter"] == [10.0, 20.0, 30.0, 40.0]
+    widths = hi - lo + 1
+    assert widths[3] < widths[0] and lo[0] == 0 and hi[-1] == 64
+    with pytest.raises(ValueError):
+        BL.late_balanced_windows(pre, 4, it_from=3, it_to=3)
