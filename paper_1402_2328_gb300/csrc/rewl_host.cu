@@ -1165,9 +1165,12 @@ int rewl_restore(rewl_t r, const char *path)
     for (int w = 0; w < r->h; ++w)
         if (lohi[w] != r->lo[w] || lohi[r->h + w] != r->hi[w])
             return r->fail(REWL_ERR_INVALID_ARG, "checkpoint window layout differs");
-    // run mode and (E, M) measurement as they were when the checkpoint was written
-    int rc = rewl_set_param(r, "measure_em", hd.has_hem ? 1.0 : 0.0);
-    if (rc != REWL_OK && !(rc == REWL_ERR_INVALID_ARG && !hd.has_hem)) return rc;
+    // run mode and (E, M) measurement as they were when the checkpoint was written (the
+    // measurement exists for the Ising model only)
+    if (r->model == 0) {
+        const int rc = rewl_set_param(r, "measure_em", hd.has_hem ? 1.0 : 0.0);
+        if (rc != REWL_OK) return rc;
+    }
     if (hd.has_hem) fields.back().dev = r->st.hem;
     size_t i = 0;
     for (const Field &f : fields) {
