@@ -43,6 +43,13 @@ WORKLOADS = {
                                 lnf_final=1e-8, flatness=0.8, interval=10_000, config_id=5),
     "ising_L8_h4_m1": dict(model=0, L=8, windows=4, walkers=1, overlap=0.75,
                            lnf_final=1e-6, flatness=0.8, interval=10_000, config_id=1),
+    # accuracy against the exact g(E) with more walkers per window (--full-run)
+    "ising_L8_h4_m128": dict(model=0, L=8, windows=4, walkers=128, overlap=0.75, lnf_final=1e-8,
+                             flatness=0.8, interval=10_000, config_id=1, seed_instance=108),
+    "ising_L16_h8_m64": dict(model=0, L=16, windows=8, walkers=64, overlap=0.75, lnf_final=1e-8,
+                             flatness=0.8, interval=10_000, config_id=1, seed_instance=116),
+    "ising_L32_h32_m16": dict(model=0, L=32, windows=32, walkers=16, overlap=0.75, lnf_final=1e-8,
+                              flatness=0.8, interval=10_000, config_id=1, seed_instance=132),
     # 24 uneven instances in one launch per round: (model, L) cycles Ising 16/32/64 and
     # q=10 Potts 20/40; windows [8,16,32,64][i%4]; walkers [4,8,16][(i//4)%3]; 6720 walkers
     "batch24_uneven": dict(batch=True, interval=10_000, config_id=4, lnf_final=1e-8,
@@ -367,8 +374,8 @@ def run_full(args, wl):
     torch.cuda.set_device(0)
     lnf_final = args.lnf_final if args.lnf_final else wl["lnf_final"]
     r = R.REWL(wl["model"], wl["L"], wl["windows"], wl["overlap"], wl["walkers"], lnf_final,
-               wl["flatness"], seed=seed_for(wl["config_id"]), interval=wl["interval"],
-               lnf_init=args.lnf_init, schedule=args.schedule)
+               wl["flatness"], seed=seed_for(wl["config_id"], wl.get("seed_instance", 0)),
+               interval=wl["interval"], lnf_init=args.lnf_init, schedule=args.schedule)
     t0 = time.perf_counter()
     r.init()
     t_init = time.perf_counter() - t0
@@ -520,7 +527,7 @@ def run_warm(args):
     per_seed = {}
     for si in range(args.warm_seeds):
         for kind in args.warm_variants.split(","):
-            res, lng = target(seed_for(5, 1 + si), kind)
+            res, lng = target(seed_for(args.warm_seed_config, args.warm_seed_offset + si), kind)
             per_seed.setdefault(kind, []).append((res, lng))
     for kind, lst in per_seed.items():
         results[kind], lngs[kind] = lst[0]
@@ -901,6 +908,9 @@ def main():
     ap.add_argument("--speedup-seeds", type=int, default=8)
     ap.add_argument("--speedup-interval", type=int, default=10_000)
     ap.add_argument("--warm-seeds", type=int, default=1, help="target runs per variant")
+    ap.add_argument("--warm-seed-config", type=int, default=5,
+                    help="target seeds: seed_for(config, offset + i), i < --warm-seeds")
+    ap.add_argument("--warm-seed-offset", type=int, default=1)
     ap.add_argument("--warm-variants", default="cold,warm",
                     help="comma list of cold | warm | cold_lw | warm_eq (lw: learned windows) | "
                          "cold_bal | warm_bal (first-iteration balanced) | cold_late | warm_late "
